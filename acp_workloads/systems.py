@@ -1,0 +1,165 @@
+"""Seeded synthetic model systems (atoms, grids, kernel strength) and the random sketch.
+
+This module draws random numbers and lays out geometry; it holds none of the
+polarizability / Sternheimer / compression / Dyson / Hessian arithmetic, so the
+CPU oracle and the CUDA path can both take their inputs from it.
+
+Model (Sec. 4.1, Eq. 1DHamil and Eq. yukawa): atoms carry Gaussian pseudocharges
+m_I(x) = -Z_I / sqrt(2 pi sigma^2) exp(-x^2 / 2 sigma^2) and interact through the
+Yukawa kernel, whose Fourier symbol is Khat(k) = 4 pi s / (|k|^2 + kappa^2) with
+s = 1/eps0 (times an optional depth scaling).  Atomic units throughout.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import numpy as np
+
+BASE_SEED = 160508021
+
+
+@dataclasses.dataclass(frozen=True)
+class System:
+    """One periodic model system.
+
+    dim       : 1 or 2
+    n         : grid points per axis (x fastest)
+    L         : box lengths per axis (bohr)
+    R         : (n_atoms, dim) atom positions in [0, L)
+    Z         : (n_atoms,) nuclear charges
+    sigma     : (n_atoms,) Gaussian widths of the pseudocharges
+    mass      : (n_atoms,) nuclear masses (1 = dynamical matrix is the Hessian)
+    kappa     : Yukawa screening parameter
+    scale     : prefactor s of Khat = 4 pi s / (k^2 + kappa^2)  (s = 1/eps0)
+    occ       : occupation f per orbital (rho = f sum_i psi_i^2)
+    name      : label
+    """
+    name: str
+    dim: int
+    n: tuple
+    L: tuple
+    R: np.ndarray
+    Z: np.ndarray
+    sigma: np.ndarray
+    mass: np.ndarray
+    kappa: float
+    scale: float
+    occ: int
+
+    @property
+    def n_atoms(self) -> int:
+        return int(self.Z.shape[0])
+
+    @property
+    def n_grid(self) -> int:
+        return int(np.prod(self.n))
+
+    @property
+    def n_pert(self) -> int:
+        return self.dim * self.n_atoms
+
+    @property
+    def n_elec(self) -> int:
+        return int(round(float(np.sum(self.Z))))
+
+    @property
+    def n_orb(self) -> int:
+        ne = self.n_elec
+        if ne % self.occ:
+            raise ValueError(f"{self.name}: {ne} electrons cannot fill orbitals of occupation {self.occ}")
+        return ne // self.occ
+
+    @property
+    def h(self) -> tuple:
+        return tuple(Li / ni for Li, ni in zip(self.L, self.n))
+
+    @property
+    def dV(self) -> float:
+        return float(np.prod(self.h))
+
+    def key(self) -> str:
+        """Stable identifier of the geometry and parameters (for the ground-state cache)."""
+        import hashlib
+        m = hashlib.sha256()
+        for a in (self.dim, self.n, self.L, self.kappa, self.scale, self.occ):
+            m.update(repr(a).encode())
+        for arr in (self.R, self.Z, self.sigma):
+            m.update(np.ascontiguousarray(arr, dtype=np.float64).tobytes())
+        return f"{self.name}-{m.hexdigest()[:12]}"
+
+
+def _rng(config: int, system: int = 0) -> np.random.Generator:
+    return np.random.default_rng(BASE_SEED + 1000 * config + system)
+
+
+def chain_1d(name, n_atoms, spacing, Z, sigma, kappa, scale, n_grid, occ, displacement=0.0, rng=None,
+             mass=1.0) -> System:
+    """Periodic 1D chain: atom I sits at (I + 1/2) * spacing plus a uniform displacement."""
+    L = n_atoms * spacing
+    R = (np.arange(n_atoms) + 0.5) * spacing
+    if displacement:
+        R = R + rng.uniform(-displacement, displacement, n_atoms)
+    Z = np.broadcast_to(np.asarray(Z, dtype=np.float64), (n_atoms,)).copy()
+    return System(name=name, dim=1, n=(int(n_grid),), L=(float(L),), R=R.reshape(n_atoms, 1),
+                  Z=Z, sigma=np.full(n_atoms, float(sigma)), mass=np.full(n_atoms, float(mass)),
+                  kappa=float(kappa), scale=float(scale), occ=int(occ))
+
+
+def paper_chain(n_atoms=60, eps0=1.0, n_grid=None) -> System:
+    """The 1D test system of Sec. 4.1: spacing 2.4, kappa 0.1, Z = 1, sigma 0.3, eps0 = 1 or 10."""
+    if n_grid is None:
+        n_grid = 10 * n_atoms * 12 // 5  # h = 0.1
+    return chain_1d(f"paper1d_na{n_atoms}_eps{eps0:g}", n_atoms, 2.4, 1.0, 0.3, 0.1, 1.0 / eps0,
+                    n_grid, occ=1)
+
+
+def config(index: int) -> System:
+    """The benchmark configurations (1-based index, 1D ones; 2D ones are not built).
+
+    1: 8 atoms every 10 bohr (L = 80), Z = 2, sigma = 1, kappa = 0.01, N = 320, occupation 2.
+    2: 128 atoms every 10 bohr with uniform +-0.5 displacements, Z uniform in {1, 2}, sigma = 1,
+       kappa = 0.01, N = 5120, occupation 1, kernel strength s = 0.5 (the small-gap end of the
+       depth-scaling range 0.5-1.0; gap 0.2435).
+    """
+    if index == 1:
+        return chain_1d("chain8_z2", 8, 10.0, 2.0, 1.0, 0.01, 1.0, 320, occ=2)
+    if index == 2:
+        rng = _rng(2)
+        disp = rng.uniform(-0.5, 0.5, 128)
+        Z = rng.integers(1, 3, 128).astype(np.float64)
+        R = ((np.arange(128) + 0.5) * 10.0 + disp).reshape(128, 1)
+        return System(name="chain128_mixed", dim=1, n=(5120,), L=(1280.0,), R=R, Z=Z,
+                      sigma=np.ones(128), mass=np.ones(128), kappa=0.01, scale=0.5, occ=1)
+    raise ValueError(f"configuration {index} is not available")
+
+
+def small_chain(n_atoms=4, n_grid=160, seed=0, mixed=True, displacement=0.3, spacing=10.0, occ=1,
+                scale=1.0) -> System:
+    """Small random chains for parity tests (several tiles and a ragged tail at small sizes)."""
+    rng = _rng(90, seed)
+    Z = rng.integers(1, 3, n_atoms).astype(np.float64) if mixed else np.full(n_atoms, 2.0)
+    if occ == 2 and int(Z.sum()) % 2:
+        Z[0] = 3.0 - Z[0]
+    sysm = chain_1d(f"small{n_atoms}_{n_grid}_s{seed}", n_atoms, spacing, Z, 1.0, 0.01, scale,
+                    n_grid, occ=occ, displacement=displacement, rng=rng)
+    return sysm
+
+
+def srft_sketch(n_cols: int, r: int, seed: int) -> np.ndarray:
+    """Real form of the subsampled randomized Fourier transform applied to G (Alg. 2 step 1, Remark).
+
+    Column nu of the SRFT is sum_j exp(-2 pi i j nu / n) eta_j e_j with |eta_j| = 1 random; r
+    distinct frequencies nu are drawn.  Its real and imaginary parts give 2r real columns, so the
+    returned Omega has shape (n_cols, 2r) (column-major friendly) and G_tilde = G @ Omega.
+    """
+    rng = np.random.default_rng(BASE_SEED + 7919 * seed + 17)
+    u = rng.uniform(0.0, 1.0, n_cols)
+    nus = rng.choice(n_cols, size=min(r, n_cols), replace=False)
+    j = np.arange(n_cols)
+    om = np.empty((n_cols, 2 * len(nus)))
+    for t, nu in enumerate(nus):
+        ph = 2.0 * np.pi * (u - j * nu / n_cols)
+        om[:, 2 * t] = np.cos(ph)
+        om[:, 2 * t + 1] = np.sin(ph)
+    return om / np.sqrt(n_cols)

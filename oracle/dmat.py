@@ -1,0 +1,31 @@
+"""Dynamical matrix and phonon frequencies (oracle side).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Eq. SecDeriv: d^2E/dR_I dR_J = int g_I (chi g_J) + delta_IJ int rho d^2V_I/dR_I^2 + d^2E_II/dR_I dR_J,
+with chi g_J = U_J from the Dyson equation (Eq. chiterm).  D_IJ = that / sqrt(M_I M_J) and
+D u_k = omega_k^2 u_k (Sec. 2.2).  Frequencies of negative eigenvalues are reported as
+-sqrt(|lambda|).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def dynamical_matrix(model, U, symmetrize=True):
+    G, _ = model.perturbations()
+    D2 = model.second_derivatives()
+    Hm = (G.T @ U) * model.h
+    Hm = Hm + np.diag(D2.T @ model.rho * model.h)
+    Hm = Hm + model.ion_hessian()
+    mass = model.sys.mass
+    D = Hm / np.sqrt(np.outer(mass, mass))
+    asym = np.linalg.norm(D - D.T) / max(np.linalg.norm(D), 1e-300)
+    if symmetrize:
+        D = 0.5 * (D + D.T)
+    return D, float(asym)
+
+
+def phonons(D):
+    lam, modes = np.linalg.eigh(0.5 * (D + D.T))
+    return np.sign(lam) * np.sqrt(np.abs(lam)), modes

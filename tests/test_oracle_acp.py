@@ -1,0 +1,93 @@
+"""Pins of the oracle's ACP steps (Alg. 2-4, Eq. LagPoly, Eq. eqnW)."""
+import numpy as np
+import pytest
+
+import acp_workloads as W
+from oracle import acp as A
+from oracle import chi0 as C
+from oracle import dyson as Dy
+from oracle.model import Model1D
+
+
+@pytest.fixture(scope="module")
+def small():
+    s = W.small_chain(4, 160, 0)
+    gs = W.ground_state(s, use_cache=False)
+    m = Model1D(s, gs)
+    Cm = C.chi0_matrix_sos(m)
+    G, B = m.perturbations()
+    return s, gs, m, Cm, G
+
+
+def test_chebyshev_nodes_are_mapped_roots():
+    nodes = A.chebyshev_nodes(-2.0, 1.0, 7)
+    # roots of T_7 mapped affinely to [-2, 1]
+    t = (2 * nodes - (-2.0 + 1.0)) / (1.0 - (-2.0))
+    assert np.allclose(np.cos(7 * np.arccos(t)), 0, atol=1e-12)
+    assert np.all(nodes > -2.0) and np.all(nodes < 1.0)
+    assert A.chebyshev_nodes(0.3, 0.3, 5).size == 1
+
+
+def test_lagrange_partition_of_unity_and_exactness():
+    nodes = A.chebyshev_nodes(-1.3, 0.4, 9)
+    x = np.linspace(-1.3, 0.4, 41)
+    Lw = A.lagrange_weights(nodes, x)
+    assert np.allclose(Lw.sum(axis=0), 1.0, atol=1e-12)
+    rng = np.random.default_rng(0)
+    for deg in range(9):
+        p = rng.standard_normal(deg + 1)
+        assert np.allclose(np.polyval(p, nodes) @ Lw, np.polyval(p, x), atol=1e-10)
+    assert np.allclose(A.lagrange_weights(nodes, nodes), np.eye(9), atol=1e-13)
+
+
+def test_interpolative_decomposition_properties(small):
+    """Xi(r_mu, :) = I; the ID reproduces M_ij = psi_i g_j within the threshold (Eq. MID)."""
+    s, gs, m, Cm, G = small
+    Om = W.srft_sketch(G.shape[1], 8, 0)
+    for eps in (1e-3, 1e-6):
+        comp = A.interpolative_decomposition(m, G, Om, eps)
+        assert np.allclose(comp.Xi[comp.pivots, :], np.eye(comp.pivots.size), atol=1e-12)
+        assert np.all(np.diff(comp.Rdiag[: comp.pivots.size]) <= 1e-12 * comp.Rdiag[0])
+        M = (m.psi[:, :, None] * G[:, None, :]).reshape(m.N, -1)
+        Mrec = comp.Xi @ M[comp.pivots, :]
+        assert np.linalg.norm(M - Mrec) <= 100 * eps * np.linalg.norm(M)
+    # full numerical rank of M_ij = psi_i * g_j is N_e * N_p here
+    comp = A.interpolative_decomposition(m, G, Om, 1e-12)
+    assert comp.pivots.size == m.n_orb * G.shape[1]
+
+
+def test_compressed_chi0_converges_to_dfpt(small):
+    """Alg. 3 approaches Alg. 1 as eps -> 0 and N_c grows (Sec. 4.1, Table 1 trend)."""
+    s, gs, m, Cm, G = small
+    U0 = Cm @ G * m.h
+    Om = W.srft_sketch(G.shape[1], 8, 0)
+    errs = []
+    for eps, nc in ((1e-2, 4), (1e-4, 10), (1e-8, 24)):
+        Ua = A.chi0_acp_apply(m, G, Om, eps, nc)
+        errs.append(np.linalg.norm(Ua - U0) / np.linalg.norm(U0))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-9
+
+
+def test_exact_compression_gives_exact_chi0(small):
+    """With full rank and W from exact eigenpairs, W Pi^T G equals chi0 G (Eq. eqnW, Eq. chi0gcompress)."""
+    s, gs, m, Cm, G = small
+    Om = W.srft_sketch(G.shape[1], 8, 0)
+    comp = A.interpolative_decomposition(m, G, Om, 1e-13)
+    # zeta(eps_i) exactly, through Lagrange interpolation at the eigenvalues themselves
+    nodes = m.eps.copy()
+    zetas = A.compressed_solves(m, comp.Xi, nodes)
+    Wm = A.build_W(m, zetas, nodes, comp.pivots)
+    U0 = Cm @ G * m.h
+    assert np.linalg.norm(Wm @ G[comp.pivots] - U0) <= 1e-9 * np.linalg.norm(U0)
+
+
+def test_adaptive_iteration_improves_on_first_iterate(small):
+    """Alg. 4: the error after several iterations is far below the error after one (Sec. 4.1)."""
+    s, gs, m, Cm, G = small
+    Ud = Dy.dyson_dense(m, G, Cm)
+    Om = W.srft_sketch(G.shape[1], 8, 0)
+    hist = []
+    A.chi_acp(m, G, Om, 1e-10, 24, delta=1e-12, maxit=6, history=hist)
+    errs = [np.linalg.norm(h["U"] - Ud) / np.linalg.norm(Ud) for h in hist]
+    assert errs[0] > 100 * errs[-1]

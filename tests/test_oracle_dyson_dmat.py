@@ -1,0 +1,84 @@
+"""Pins of the oracle's Dyson solve and dynamical matrix (Eq. dyson, Eq. SecDeriv)."""
+import numpy as np
+import pytest
+
+import acp_workloads as W
+from oracle import chi0 as C
+from oracle import dmat as Dm
+from oracle import dyson as Dy
+from oracle.model import Model1D
+
+
+@pytest.fixture(scope="module")
+def small():
+    s = W.small_chain(4, 160, 0)
+    gs = W.ground_state(s, use_cache=False)
+    m = Model1D(s, gs)
+    Cm = C.chi0_matrix_sos(m)
+    return s, gs, m, Cm
+
+
+def test_gmres_equals_dense_dyson(small):
+    s, gs, m, Cm = small
+    G, _ = m.perturbations()
+    Ud = Dy.dyson_dense(m, G, Cm)
+    Ug, k = Dy.dyson_gmres(m, G, chi0=lambda X: Cm @ X * m.h, tol=1e-13)
+    assert np.linalg.norm(Ug - Ud) <= 1e-10 * np.linalg.norm(Ud)
+
+
+def test_chi_symmetric_nsd_and_weak_coupling_limit(small):
+    """chi = (I - chi0 K)^-1 chi0 is symmetric negative semidefinite; K -> 0 gives chi = chi0."""
+    s, gs, m, Cm = small
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((m.N, 5))
+    U = Dy.dyson_dense(m, X, Cm)
+    Mq = X.T @ U * m.h
+    assert np.allclose(Mq, Mq.T, atol=1e-9 * np.abs(Mq).max())
+    assert np.linalg.eigvalsh(0.5 * (Mq + Mq.T)).max() <= 1e-9 * np.abs(Mq).max()
+    m0 = Model1D(s, gs)
+    m0.khat = m0.khat * 1e-14
+    U0 = Dy.dyson_dense(m0, X, Cm)
+    assert np.allclose(U0, Cm @ X * m.h, atol=1e-9 * np.abs(U0).max())
+
+
+def test_dynamical_matrix_symmetry_and_acoustic_sum_rule(small):
+    s, gs, m, Cm = small
+    G, _ = m.perturbations()
+    D, asym = Dm.dynamical_matrix(m, Dy.dyson_dense(m, G, Cm))
+    assert asym < 1e-8
+    assert np.abs(D.sum(axis=1)).max() <= 1e-6 * np.linalg.norm(D)
+
+
+def _bonded(R=None):
+    rng = np.random.default_rng(11)
+    s = W.chain_1d("bonded", 4, 3.0, 1.0, 0.5, 0.1, 1.0, 96, occ=1, displacement=0.15, rng=rng)
+    if R is not None:
+        s = W.System(**{**s.__dict__, "R": R})
+    return s
+
+
+def _forces(R, V_start=None):
+    s = _bonded(R)
+    gs = W.ground_state(s, use_cache=False, tol=1e-14, maxit=300, V_start=V_start)
+    return Model1D(s, gs).forces(), gs
+
+
+def test_dynamical_matrix_equals_frozen_phonon_differences():
+    """D from DFPT equals central differences of Hellmann-Feynman forces (Sec. 1, Eq. force)."""
+    s = _bonded()
+    gs = W.ground_state(s, use_cache=False, tol=1e-14, maxit=300)
+    m = Model1D(s, gs)
+    G, _ = m.perturbations()
+    D, _ = Dm.dynamical_matrix(m, Dy.dyson_dense(m, G))
+    Dfd = np.zeros_like(D)
+    for J in range(s.n_atoms):
+        cols = []
+        for d in (2e-3, 1e-3):
+            Rp, Rm = s.R.copy(), s.R.copy()
+            Rp[J, 0] += d
+            Rm[J, 0] -= d
+            Fp, _ = _forces(Rp, gs.V)
+            Fm, _ = _forces(Rm, gs.V)
+            cols.append(-(Fp - Fm) / (2 * d))
+        Dfd[:, J] = (4 * cols[1] - cols[0]) / 3.0
+    assert np.linalg.norm(D - Dfd) <= 1e-6 * np.linalg.norm(D)
