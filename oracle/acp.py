@@ -90,7 +90,8 @@ def compressed_solves(model, Xi, nodes, tol=1e-12, maxit=5000, chunk=2048):
         Z = np.empty_like(RHS)
         for s0 in range(0, n_mu, chunk):
             sl = slice(s0, min(n_mu, s0 + chunk))
-            Z[:, sl] = -minres(A, RHS[:, sl], np.full(sl.stop - sl.start, ec), tol=tol, maxit=maxit)
+            X = minres(A, RHS[:, sl], np.full(sl.stop - sl.start, ec), tol=tol, maxit=maxit, keep=model.project)
+            Z[:, sl] = -model.project(X)  # zeta lies in the unoccupied space (Eq. eqncompressU)
         Zs.append(Z)
     return Zs
 

@@ -46,9 +46,10 @@ def chi0_apply(model, G, tol=1e-12, maxit=5000, chunk=2048, return_info=False):
         # rounding residue must not be solved for
         tiny = np.linalg.norm(R, axis=0) <= 1e-13 * np.linalg.norm(P, axis=0)
         R[:, tiny] = 0.0
-        X, info = minres(A, R, model.eps[i], tol=tol, maxit=maxit, return_info=True)
+        X, info = minres(A, R, model.eps[i], tol=tol, maxit=maxit, return_info=True, keep=model.project)
         its.append(info["iterations"])
-        Z = -X
+        # the outer Q of Eq. Sternheimer: the solution lies in the unoccupied space
+        Z = -model.project(X)
         contrib = 2.0 * model.f * model.psi[:, i] * Z
         np.add.at(U.T, j, contrib.T)
     if return_info:

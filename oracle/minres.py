@@ -10,13 +10,19 @@ coefficients (alpha_k, beta_k); Givens rotations factor that tridiagonal matrix 
 give the residual norm |phibar| for free; the iterate is updated through direction vectors
 w_k = (v_k - eps_k w_{k-2} - delta_k w_{k-1}) / gamma_k.  A column stops when
 |phibar| <= tol * ||b||; converged columns are frozen.
+
+``keep`` (optional) maps each new Lanczos vector back into a subspace the operator must not
+leave.  For the projected Sternheimer operator Q(H - s)Q the occupied space is its null space:
+rounding puts tiny occupied components into every Lanczos vector, and the three-term recurrence
+multiplies them by the Lanczos polynomials evaluated at 0, which lies outside the spectrum and
+grows geometrically with the iteration count.  Projecting each new vector with Q removes them.
 """
 from __future__ import annotations
 
 import numpy as np
 
 
-def minres(apply_A, B, shifts, tol=1e-12, maxit=5000, return_info=False):
+def minres(apply_A, B, shifts, tol=1e-12, maxit=5000, return_info=False, keep=None):
     """Solve (A - shifts[j]) X[:, j] = B[:, j] for every column j.
 
     apply_A(V, s) must return A V - s V column-wise for V of shape (N, m) and s of shape (m,).
@@ -51,6 +57,8 @@ def minres(apply_A, B, shifts, tol=1e-12, maxit=5000, return_info=False):
             P -= beta_prev_used[idx] * V_prev[:, idx]
         alpha = np.einsum("ij,ij->j", v, P)
         P -= alpha * v
+        if keep is not None:
+            P = keep(P)
         beta_next = np.linalg.norm(P, axis=0)
         # Givens QR of the growing tridiagonal matrix
         oldeps = epsln[idx]

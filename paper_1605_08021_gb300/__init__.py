@@ -1,0 +1,7 @@
+"""GB300 (sm_103a) library for the adaptively compressed polarizability operator (arXiv:1605.08021).
+
+The compute path is ``libacp.so`` (CUDA kernels behind the C ABI of ``include/acp.h``); this
+package holds its build script and a ctypes binding that only marshals arguments.
+"""
+from .binding import (ACP_METHOD_ACP, ACP_METHOD_PLAIN, AcpError, Context, declared_symbols,  # noqa: F401
+                      load, options)

@@ -1,0 +1,329 @@
+"""ctypes binding of libacp (include/acp.h): argument marshalling only.
+
+Blocks of grid functions are torch CUDA tensors of shape (ncol, N), float64, contiguous: row j is
+grid function j, which is the column-major N x ncol layout of the C ABI.  Every computation runs
+in the library's CUDA kernels; there is no fallback: a missing library raises at import of the
+first context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from ctypes import POINTER, c_double, c_int, c_longlong, c_void_p
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libacp.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "acp.h")
+
+ACP_METHOD_PLAIN = 0
+ACP_METHOD_ACP = 1
+
+STATUS = {0: "ACP_OK", 1: "ACP_E_ARG", 2: "ACP_E_CUDA", 3: "ACP_E_OOM", 4: "ACP_E_NOCONV",
+          5: "ACP_E_TIMEOUT", 6: "ACP_E_GAP", 7: "ACP_E_RANK", 8: "ACP_E_NUMERIC"}
+
+
+class AcpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("n", c_int * 2), ("L", c_double * 2)]
+
+
+class Kernel(ctypes.Structure):
+    _fields_ = [("kappa", c_double), ("scale", c_double)]
+
+
+class Atoms(ctypes.Structure):
+    _fields_ = [("n_atoms", c_int), ("R", POINTER(c_double)), ("Z", POINTER(c_double)),
+                ("sigma", POINTER(c_double)), ("mass", POINTER(c_double))]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("method", c_int), ("occ", c_double), ("n_cheb", c_int), ("id_tol", c_double),
+                ("sketch_cols", c_int), ("sketch", POINTER(c_double)), ("max_rank", c_int),
+                ("stern_tol", c_double), ("stern_maxit", c_int), ("dyson_tol", c_double),
+                ("dyson_maxit", c_int), ("rhs_batch", c_int), ("deadline_s", c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_mu", c_int), ("outer_iters", c_int), ("rhs_solved", c_longlong),
+                ("lanczos_steps", c_longlong), ("max_iters", c_longlong), ("max_rel_res", c_double),
+                ("ms_solve", c_double), ("ms_compress", c_double), ("ms_total", c_double),
+                ("asymmetry", c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def declared_symbols():
+    """Names of the functions declared in include/acp.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(acp_[a-z0-9_]+)\s*\(", text)))
+
+
+def load():
+    """Load libacp.so (built in-tree by ``paper_1605_08021_gb300.build``); raise if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libacp.so is not built ({LIB_PATH}); run python -m paper_1605_08021_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, D, I = c_void_p, POINTER(c_double), c_int
+    sig = {
+        "acp_options_default": (None, [POINTER(Options)]),
+        "acp_init": (I, [POINTER(P), POINTER(Grid), POINTER(Kernel), P, P, D, I, POINTER(Options), P]),
+        "acp_set_options": (I, [P, POINTER(Options)]),
+        "acp_apply_chi0": (I, [P, P, I, P, POINTER(Stats)]),
+        "acp_dyson_solve": (I, [P, P, I, P, POINTER(Stats)]),
+        "acp_perturbations": (I, [P, POINTER(Atoms), P, P, P]),
+        "acp_dynamical_matrix": (I, [P, POINTER(Atoms), P, D, P, POINTER(Stats)]),
+        "acp_phonons": (I, [P, D, I, D, D]),
+        "acp_hamiltonian_apply": (I, [P, P, I, D, P]),
+        "acp_project": (I, [P, P, I, P]),
+        "acp_kernel_apply": (I, [P, P, I, I, P]),
+        "acp_sternheimer_solve": (I, [P, P, I, D, P, POINTER(Stats)]),
+        "acp_compress": (I, [P, P, I, I, POINTER(c_int), POINTER(c_int), P, D]),
+        "acp_update": (I, [P, P, P, D, I]),
+        "acp_profile_enable": (I, [P, I]),
+        "acp_profile_get": (I, [P, ctypes.c_char_p, D, POINTER(c_longlong), D, D]),
+        "acp_launch_count": (c_longlong, [P]),
+        "acp_destroy": (None, [P]),
+        "acp_last_error": (ctypes.c_char_p, [P]),
+        "acp_status_string": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+def _tptr(t):
+    return c_void_p(t.data_ptr())
+
+
+def _check_block(t, N, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.dim() != 2 or t.shape[1] != N:
+        raise ValueError(f"{name} must have shape (ncol, {N}), got {tuple(t.shape)}")
+
+
+def options(method=ACP_METHOD_ACP, occ=1.0, n_cheb=16, id_tol=1e-5, sketch=None, max_rank=0,
+            stern_tol=1e-11, stern_maxit=5000, dyson_tol=1e-10, dyson_maxit=30, rhs_batch=0,
+            deadline_s=0.0):
+    """Options as a dict (the sketch Omega, if given, is an (n_cols, r) float64 array)."""
+    return dict(method=method, occ=occ, n_cheb=n_cheb, id_tol=id_tol, sketch=sketch, max_rank=max_rank,
+                stern_tol=stern_tol, stern_maxit=stern_maxit, dyson_tol=dyson_tol, dyson_maxit=dyson_maxit,
+                rhs_batch=rhs_batch, deadline_s=deadline_s)
+
+
+class Context:
+    """One acp_ctx bound to the current torch CUDA stream."""
+
+    def __init__(self, n_grid, L, kappa, scale, V, psi, eps, opts=None, stream=None):
+        import torch
+        self.lib = load()
+        self.N = int(n_grid)
+        self.L = float(L)
+        self.h = self.L / self.N
+        self.n_orb = int(psi.shape[0])
+        _check_block(psi, self.N, "psi")
+        if not (V.is_cuda and V.dtype == torch.float64 and V.is_contiguous() and V.numel() == self.N):
+            raise TypeError("V must be a contiguous float64 CUDA vector of length N")
+        self._eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64)[: self.n_orb])
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        self._opts = None
+        self._sketch = None
+        o = self._make_options(opts or options())
+        g = Grid(1, (c_int * 2)(self.N, 0), (c_double * 2)(self.L, 0.0))
+        k = Kernel(float(kappa), float(scale))
+        ptr = c_void_p()
+        st = self.lib.acp_init(ctypes.byref(ptr), ctypes.byref(g), ctypes.byref(k), _tptr(V), _tptr(psi),
+                               _dptr(self._eps), self.n_orb, ctypes.byref(o), c_void_p(self.stream.cuda_stream))
+        self.ptr = ptr
+        if st != 0:
+            msg = self.lib.acp_last_error(ptr).decode() if ptr.value else "acp_init failed"
+            if ptr.value:
+                self.lib.acp_destroy(ptr)
+                self.ptr = c_void_p()
+            raise AcpError(st, msg)
+
+    def _make_options(self, d):
+        o = Options()
+        o.method = int(d["method"])
+        o.occ = float(d["occ"])
+        o.n_cheb = int(d["n_cheb"])
+        o.id_tol = float(d["id_tol"])
+        sk = d.get("sketch")
+        if sk is not None:
+            self._sketch = np.asfortranarray(np.asarray(sk, dtype=np.float64))
+            o.sketch_cols = int(self._sketch.shape[1])
+            o.sketch = self._sketch.ctypes.data_as(POINTER(c_double))
+        else:
+            self._sketch = None
+            o.sketch_cols = 0
+            o.sketch = None
+        o.max_rank = int(d["max_rank"])
+        o.stern_tol = float(d["stern_tol"])
+        o.stern_maxit = int(d["stern_maxit"])
+        o.dyson_tol = float(d["dyson_tol"])
+        o.dyson_maxit = int(d["dyson_maxit"])
+        o.rhs_batch = int(d["rhs_batch"])
+        o.deadline_s = float(d["deadline_s"])
+        self._opts = o
+        return o
+
+    def set_options(self, **kw):
+        d = {k: getattr(self._opts, k) for k, _ in Options._fields_ if k not in ("sketch", "sketch_cols")}
+        d["sketch"] = self._sketch
+        d.update(kw)
+        o = self._make_options(d)
+        self._call(self.lib.acp_set_options(self.ptr, ctypes.byref(o)))
+
+    def _call(self, st, allow_noconv=False):
+        if st == 0 or (allow_noconv and st == 4):
+            return st
+        raise AcpError(st, self.lib.acp_last_error(self.ptr).decode())
+
+    def close(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            self.lib.acp_destroy(self.ptr)
+            self.ptr = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- entry points -----------------------------------------------------------------------
+    def update(self, V, psi, eps):
+        _check_block(psi, self.N, "psi")
+        self._eps = np.ascontiguousarray(np.asarray(eps, dtype=np.float64)[: self.n_orb])
+        self._call(self.lib.acp_update(self.ptr, _tptr(V), _tptr(psi), _dptr(self._eps), self.n_orb))
+
+    def profile(self, enable=True):
+        self._call(self.lib.acp_profile_enable(self.ptr, int(bool(enable))))
+
+    def profile_get(self, kernel):
+        ms, fl, by = c_double(0), c_double(0), c_double(0)
+        n = c_longlong(0)
+        self._call(self.lib.acp_profile_get(self.ptr, kernel.encode(), ctypes.byref(ms), ctypes.byref(n),
+                                            ctypes.byref(fl), ctypes.byref(by)))
+        return dict(ms=ms.value, launches=n.value, flops=fl.value, bytes=by.value)
+
+    def launch_count(self):
+        return int(self.lib.acp_launch_count(self.ptr))
+
+    def _out(self, ncol):
+        import torch
+        return torch.empty((ncol, self.N), dtype=torch.float64, device="cuda")
+
+    def apply_chi0(self, G, out=None):
+        _check_block(G, self.N, "G")
+        out = self._out(G.shape[0]) if out is None else out
+        st = Stats()
+        self._call(self.lib.acp_apply_chi0(self.ptr, _tptr(G), G.shape[0], _tptr(out), ctypes.byref(st)))
+        return out, st.as_dict()
+
+    def dyson_solve(self, G, out=None, allow_noconv=False):
+        _check_block(G, self.N, "G")
+        out = self._out(G.shape[0]) if out is None else out
+        st = Stats()
+        self._call(self.lib.acp_dyson_solve(self.ptr, _tptr(G), G.shape[0], _tptr(out), ctypes.byref(st)),
+                   allow_noconv)
+        return out, st.as_dict()
+
+    def _atoms(self, R, Z, sigma, mass=None):
+        self._atom_arrays = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel())
+                             for a in (R, Z, sigma)]
+        m = None if mass is None else np.ascontiguousarray(np.asarray(mass, dtype=np.float64).ravel())
+        self._atom_arrays.append(m)
+        a = Atoms()
+        a.n_atoms = int(self._atom_arrays[1].size)
+        a.R, a.Z, a.sigma = (_dptr(x) for x in self._atom_arrays[:3])
+        a.mass = _dptr(m) if m is not None else None
+        return a
+
+    def perturbations(self, R, Z, sigma):
+        a = self._atoms(R, Z, sigma)
+        G, B, D2 = self._out(a.n_atoms), self._out(a.n_atoms), self._out(a.n_atoms)
+        self._call(self.lib.acp_perturbations(self.ptr, ctypes.byref(a), _tptr(G), _tptr(B), _tptr(D2)))
+        return G, B, D2
+
+    def dynamical_matrix(self, R, Z, sigma, rho, mass=None, U=None, allow_noconv=False):
+        a = self._atoms(R, Z, sigma, mass)
+        D = np.zeros((a.n_atoms, a.n_atoms))
+        st = Stats()
+        Up = _tptr(U) if U is not None else c_void_p()
+        self._call(self.lib.acp_dynamical_matrix(self.ptr, ctypes.byref(a), _tptr(rho), _dptr(D), Up,
+                                                 ctypes.byref(st)), allow_noconv)
+        return D, st.as_dict()
+
+    def phonons(self, D, modes=False):
+        D = np.ascontiguousarray(np.asarray(D, dtype=np.float64))
+        n = D.shape[0]
+        w = np.zeros(n)
+        M = np.zeros((n, n)) if modes else None
+        self._call(self.lib.acp_phonons(self.ptr, _dptr(D), n, _dptr(w), _dptr(M) if modes else None))
+        return (w, M.T.copy()) if modes else w
+
+    def hamiltonian_apply(self, X, shifts=None):
+        _check_block(X, self.N, "X")
+        Y = self._out(X.shape[0])
+        sh = None if shifts is None else np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+        self._call(self.lib.acp_hamiltonian_apply(self.ptr, _tptr(X), X.shape[0], _dptr(sh) if sh is not None
+                                                  else None, _tptr(Y)))
+        return Y
+
+    def project(self, X):
+        _check_block(X, self.N, "X")
+        Y = self._out(X.shape[0])
+        self._call(self.lib.acp_project(self.ptr, _tptr(X), X.shape[0], _tptr(Y)))
+        return Y
+
+    def kernel_apply(self, X, inverse=False):
+        _check_block(X, self.N, "X")
+        Y = self._out(X.shape[0])
+        self._call(self.lib.acp_kernel_apply(self.ptr, _tptr(X), X.shape[0], -1 if inverse else 1, _tptr(Y)))
+        return Y
+
+    def sternheimer_solve(self, Bm, shifts, allow_noconv=False):
+        _check_block(Bm, self.N, "B")
+        X = self._out(Bm.shape[0])
+        sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+        st = Stats()
+        self._call(self.lib.acp_sternheimer_solve(self.ptr, _tptr(Bm), Bm.shape[0], _dptr(sh), _tptr(X),
+                                                  ctypes.byref(st)), allow_noconv)
+        return X, st.as_dict()
+
+    def compress(self, G, cap=None):
+        import torch
+        _check_block(G, self.N, "G")
+        cap = cap or self.N
+        n_mu = c_int(0)
+        piv = (c_int * cap)()
+        rd = np.zeros(cap)
+        Xi = torch.empty((cap, self.N), dtype=torch.float64, device="cuda")
+        self._call(self.lib.acp_compress(self.ptr, _tptr(G), G.shape[0], cap, ctypes.byref(n_mu), piv,
+                                         _tptr(Xi), _dptr(rd)))
+        k = n_mu.value
+        return k, np.array(piv[:k], dtype=np.int64), Xi[:k], rd[:k]

@@ -1,0 +1,147 @@
+// FP64 GEMM for the projector Q = I - Psi Psi^T h (Sec. 2.2), the W construction of Eq. eqnW,
+// the products W G(r_mu, :) (Eq. chi0gcompress2) and W X (Eq. dyson4), and the dynamical matrix
+// term G^T U (Eq. SecDeriv).  tcgen05 has no FP64 kind, so this path is a register-blocked DFMA
+// kernel: 64 x 64 output tiles, 16-deep shared-memory k-slices, 4 x 4 outputs per thread.
+#include "internal.cuh"
+
+namespace acp {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+template <bool TA, bool TB, bool HAD>
+__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A,
+                                                    int lda, const double* __restrict__ B, int ldb, double beta,
+                                                    double* __restrict__ C, int ldc, const double* __restrict__ Hz,
+                                                    int ldh) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int e0 = 0; e0 < BM * BK; e0 += 256) {
+      const int e = e0 + tid;
+      int mm, kk;
+      if (!TA) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      double v = 0.0;
+      if (gm < M && gk < K) v = TA ? A[gk + (size_t)gm * lda] : A[gm + (size_t)gk * lda];
+      As[kk][mm] = v;
+    }
+#pragma unroll
+    for (int e0 = 0; e0 < BN * BK; e0 += 256) {
+      const int e = e0 + tid;
+      int nn, kk;
+      if (!TB) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
+      const int gn = n0 + nn, gk = k0 + kk;
+      double v = 0.0;
+      if (gn < N && gk < K) v = TB ? B[gn + (size_t)gk * ldb] : B[gk + (size_t)gn * ldb];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int gn = n0 + ty + 16 * j;
+    if (gn >= N) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int gm = m0 + tx + 16 * i;
+      if (gm >= M) continue;
+      double* c = &C[gm + (size_t)gn * ldc];
+      if (HAD) {
+        *c += alpha * Hz[gm + (size_t)gn * ldh] * acc[i][j];
+      } else {
+        *c = alpha * acc[i][j] + (beta == 0.0 ? 0.0 : beta * *c);
+      }
+    }
+  }
+}
+
+template <bool TA, bool TB>
+void launch(dim3 g, cudaStream_t s, int m, int n, int k, double alpha, const double* A, int lda, const double* B,
+            int ldb, double beta, double* C, int ldc, const double* hz, int ldh) {
+  if (hz)
+    dgemm_kernel<TA, TB, true><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, hz, ldh);
+  else
+    dgemm_kernel<TA, TB, false><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, hz, ldh);
+}
+
+}  // namespace
+
+acp_status dgemm(acp_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* A, int lda,
+                 const double* B, int ldb, double beta, double* C, int ldc, const double* hz, int ldhz) {
+  if (m <= 0 || n <= 0) return ACP_OK;
+  const unsigned gy = (unsigned)((n + BN - 1) / BN);
+  if (gy > 65535u) {
+    // split very wide products into column slabs (grid.y limit)
+    const int slab = 65535 * BN;
+    for (int c0 = 0; c0 < n; c0 += slab) {
+      const int nc = (n - c0 < slab) ? n - c0 : slab;
+      const double* Bp = tb ? B + c0 : B + (size_t)c0 * ldb;
+      ACP_TRY(dgemm(ctx, ta, tb, m, nc, k, alpha, A, lda, Bp, ldb, beta, C + (size_t)c0 * ldc, ldc,
+                    hz ? hz + (size_t)c0 * ldhz : nullptr, ldhz));
+    }
+    return ACP_OK;
+  }
+  dim3 g((m + BM - 1) / BM, gy);
+  if (k <= 0) {
+    // C = beta C (or unchanged for the Hadamard epilogue)
+    if (hz) return ACP_OK;
+    ::acp::note_launch(ctx);
+    launch<false, false>(g, ctx->stream, m, n, 0, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, 0);
+    ACP_LAUNCH(ctx);
+    return ACP_OK;
+  }
+  ::acp::note_launch(ctx);
+  const double e_flops = 2.0 * m * n * k;
+  const double e_bytes = 8.0 * ((double)m * k + (double)k * n + (double)m * n * ((beta != 0.0 || hz) ? 2 : 1) +
+                                (hz ? (double)m * n : 0.0));
+  cudaEvent_t ev0 = prof_begin(ctx);
+  if (!ta && !tb) launch<false, false>(g, ctx->stream, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, hz, ldhz);
+  else if (ta && !tb) launch<true, false>(g, ctx->stream, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, hz, ldhz);
+  else if (!ta && tb) launch<false, true>(g, ctx->stream, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, hz, ldhz);
+  else launch<true, true>(g, ctx->stream, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, hz, ldhz);
+  ACP_LAUNCH(ctx);
+  prof_end(ctx, "dgemm", ev0, e_flops, e_bytes);
+  return ACP_OK;
+}
+
+acp_status project(acp_ctx* ctx, const double* X, int ldx, int ncol, double* Y, int ldy) {
+  if (ncol <= 0) return ACP_OK;
+  const int N = ctx->N, no = ctx->n_orb;
+  double* C = nullptr;
+  ACP_TRY(ws(ctx, "proj_c", (size_t)no * ncol, &C));
+  // C = h Psi^T X
+  ACP_TRY(dgemm(ctx, true, false, no, ncol, N, ctx->h, ctx->d_psi, N, X, ldx, 0.0, C, no));
+  if (Y != X)
+    ACP_CUDA(ctx, cudaMemcpy2DAsync(Y, (size_t)ldy * sizeof(double), X, (size_t)ldx * sizeof(double),
+                                    (size_t)N * sizeof(double), ncol, cudaMemcpyDeviceToDevice, ctx->stream));
+  // Y -= Psi C
+  ACP_TRY(dgemm(ctx, false, false, N, ncol, no, -1.0, ctx->d_psi, N, C, no, 1.0, Y, ldy));
+  return ACP_OK;
+}
+
+}  // namespace acp

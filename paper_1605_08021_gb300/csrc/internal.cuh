@@ -1,0 +1,212 @@
+// Internal declarations of the ACP library: context, workspace, error plumbing, device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/acp.h"
+
+namespace acp {
+
+// ---- FFT plan: N = prod rad[s], radices in {2, 3, 4, 5}; threads per transform --------------
+struct FftPlan {
+  int n = 0;
+  int nst = 0;
+  int rad[24];
+  int threads = 0;  // CTA size of the spectral kernels
+};
+
+bool make_fft_plan(int n, FftPlan* plan);
+
+// ---- instrumentation: per-kernel device time from CUDA events on the context's stream --------
+struct Profiler {
+  bool on = false;
+  long long launches = 0;  // every kernel launch of the library, counted whether on or not
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+  struct Pending {
+    const char* name;
+    cudaEvent_t a, b;
+    double flops, bytes;
+  };
+  std::vector<Pending> pending;
+  struct Acc {
+    double ms = 0, flops = 0, bytes = 0;
+    long long n = 0;
+  };
+  std::map<std::string, Acc> acc;
+  ~Profiler();
+};
+
+// ---- workspace: named device buffers that grow on demand ------------------------------------
+struct Workspace {
+  std::map<std::string, std::pair<void*, size_t>> bufs;
+  ~Workspace();
+};
+
+}  // namespace acp
+
+struct acp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int N = 0;
+  double L = 0, h = 0;
+  double kappa = 0, scale = 0;
+  int n_orb = 0;
+  acp_options opt{};
+  std::vector<double> eps;        // host copy, ascending
+  double* d_V = nullptr;          // N
+  double* d_psi = nullptr;        // N x n_orb
+  double* d_eps = nullptr;        // n_orb
+  double* d_kin = nullptr;        // N: k^2/2
+  double* d_khat = nullptr;       // N: Khat(k)
+  double* d_khat_inv = nullptr;   // N: 1/Khat(k)
+  double* d_kvec = nullptr;       // N: k with the Nyquist entry zeroed (odd multipliers)
+  double2* d_tw = nullptr;        // N: exp(-2 pi i m / N)
+  int* d_flag = nullptr;          // device status word / counters (16 ints)
+  acp::FftPlan plan;
+  acp::Workspace ws;
+  acp::Profiler prof;
+  std::string err;
+};
+
+namespace acp {
+
+// ---- errors ---------------------------------------------------------------------------------
+acp_status set_error(acp_ctx* ctx, acp_status st, const char* fmt, ...);
+
+#define ACP_CUDA(ctx, call)                                                                    \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return ::acp::set_error((ctx), ACP_E_CUDA, "%s failed: %s (%s:%d)", #call,               \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+  } while (0)
+
+#define ACP_LAUNCH(ctx)                                                                        \
+  do {                                                                                         \
+    cudaError_t e_ = cudaGetLastError();                                                       \
+    if (e_ != cudaSuccess)                                                                     \
+      return ::acp::set_error((ctx), ACP_E_CUDA, "kernel launch failed: %s (%s:%d)",           \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+  } while (0)
+
+#define ACP_TRY(x)                                                                             \
+  do {                                                                                         \
+    acp_status s_ = (x);                                                                       \
+    if (s_ != ACP_OK) return s_;                                                               \
+  } while (0)
+
+// Device buffer from the context's workspace, grown (never shrunk) to hold `bytes`.
+acp_status ws_get(acp_ctx* ctx, const char* name, size_t bytes, void** out);
+template <class T>
+inline acp_status ws(acp_ctx* ctx, const char* name, size_t count, T** out) {
+  return ws_get(ctx, name, count * sizeof(T), reinterpret_cast<void**>(out));
+}
+
+double now_ms();
+bool deadline_passed(const acp_ctx* ctx, double t0_ms);
+
+inline void note_launch(acp_ctx* ctx) { ++ctx->prof.launches; }
+// Event recorded on the context's stream before a timed launch (nullptr when profiling is off).
+cudaEvent_t prof_begin(acp_ctx* ctx);
+// Records the end event of a timed launch with its algorithmic flops and bytes.
+void prof_end(acp_ctx* ctx, const char* name, cudaEvent_t begin, double flops, double bytes);
+// Accumulates the elapsed times of completed launches (the stream must be synchronised).
+void prof_flush(acp_ctx* ctx);
+
+// ---- host wrappers of the kernels (one translation unit each) -------------------------------
+// spectral.cu
+enum SpectralMult { MULT_KINETIC = 0, MULT_KHAT = 1, MULT_KHAT_INV = 2 };
+// Y[:, j] = IFFT(mult * FFT(X[:, j])) + (with_v ? V .* X[:, j] : 0) - shift_d[j] X[:, j]
+// alpha_d (nullable): alpha_d[j] = X[:, j] . Y[:, j] (no weight).  Columns with active_d[j] == 0
+// are skipped when active_d is not null.  Lanczos form (Xprev != nullptr): the output is
+// Y - alpha_j X_j - beta_d[j] Xprev_j, the unprojected next Lanczos vector.
+acp_status spectral_apply(acp_ctx* ctx, const double* X, int ldx, int ncol, SpectralMult mult, bool with_v,
+                          const double* shift_d, double* Y, int ldy, double* alpha_d, const int* active_d,
+                          const double* Xprev = nullptr, const double* beta_d = nullptr);
+// Raise the dynamic shared-memory limit of the spectral kernels (once per context).
+acp_status spectral_configure(acp_ctx* ctx);
+// Perturbation potentials of n_atoms atoms (1D): G, B, d2V (each nullable, N x n_atoms).
+acp_status perturbations_1d(acp_ctx* ctx, int n_atoms, const double* R_d, const double* Z_d, const double* sig_d,
+                            double* G, double* B, double* D2);
+
+// dgemm.cu: C = alpha op(A) op(B) + beta C (column-major).  If hz != nullptr the epilogue is
+// C += alpha * hz .* (op(A) op(B)) (Hadamard accumulate; ldhz = leading dimension).
+acp_status dgemm(acp_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alpha, const double* A, int lda,
+                 const double* B, int ldb, double beta, double* C, int ldc, const double* hz = nullptr,
+                 int ldhz = 0);
+
+// projector: Y = Q X (Y may alias X).  Columns processed in chunks through workspace "proj".
+acp_status project(acp_ctx* ctx, const double* X, int ldx, int ncol, double* Y, int ldy);
+
+// minres.cu
+struct SolveReport {
+  long long converged = 0;
+  long long steps = 0;
+  long long max_iters = 0;
+  double max_rel_res = 0;
+  bool all_converged = true;
+};
+// Solve Q(H - shift_d[j])Q X_j = B_j (B must already be projected) for ncol columns.
+acp_status minres_batched(acp_ctx* ctx, const double* B, int ncol, const double* shift_d, double* X,
+                          SolveReport* rep, double t0_ms);
+// Multi-shift: for each column mu of B solve Q(H - nodes[c])Q X_{c,mu} = B_mu for all c.
+// X layout: column mu + c * ncol of an N x (nc * ncol) block.
+acp_status minres_multishift(acp_ctx* ctx, const double* B, int ncol, const double* nodes_d, int nc, double* X,
+                             SolveReport* rep, double t0_ms);
+
+// qrcp.cu: Alg. 2 (Remark form) on G (N x ncol).  Writes n_mu, pivots (device, int), Xi (N x n_mu,
+// workspace "xi"), and |R_mm| on the host.
+struct Compression {
+  int n_mu = 0;
+  int* d_piv = nullptr;   // workspace-owned
+  double* d_xi = nullptr; // workspace-owned, N x n_mu
+  std::vector<int> piv;
+  std::vector<double> rdiag;
+};
+acp_status compress(acp_ctx* ctx, const double* G, int ncol, const double* sketch_h, int sketch_cols,
+                    double id_tol, int max_rank, Compression* out);
+
+// dense.cu: LU solve of an n x n system with nrhs right-hand sides (A, B overwritten; X in B).
+acp_status lu_solve(acp_ctx* ctx, double* A, int n, double* B, int nrhs);
+// Jacobi eigensolver of a symmetric n x n device matrix; eigenvalues (ascending) and vectors.
+acp_status jacobi_eig(acp_ctx* ctx, double* A, int n, double* w_d, double* V_d);
+// Frobenius norms: out_h[0] = ||A - B||_F^2, out_h[1] = ||A||_F^2 (N x ncol blocks)
+acp_status diff_norms(acp_ctx* ctx, const double* A, const double* B, size_t count, double* out_h);
+// small helpers
+acp_status gather_rows(acp_ctx* ctx, const double* X, int ldx, int ncol, const int* rows_d, int nrows, double* Y,
+                       int ldy);
+
+}  // namespace acp
+
+// ---- device helpers ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the CTA; every thread gets the result.  red must hold 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (wid == 0) {
+    t = warp_sum(t);
+    if (lane == 0) red[0] = t;
+  }
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}

@@ -1,0 +1,56 @@
+"""The C ABI library builds, loads without a GPU and exports every symbol include/acp.h declares;
+the ctypes structures have the C layout.  No compute call is made here."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import paper_1605_08021_gb300 as P
+from paper_1605_08021_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1605_08021_gb300.build import build
+    build()
+    return P.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = P.declared_symbols()
+    assert "acp_init" in syms and "acp_apply_chi0" in syms and "acp_phonons" in syms
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing
+
+
+def test_status_strings_and_defaults(lib):
+    assert lib.acp_status_string(0).decode() == "ok"
+    assert "rank" in lib.acp_status_string(7).decode()
+    o = B.Options()
+    lib.acp_options_default(ctypes.byref(o))
+    assert o.method == B.ACP_METHOD_ACP and o.n_cheb == 16 and o.stern_maxit == 5000
+    assert abs(o.stern_tol - 1e-11) < 1e-25
+
+
+def test_struct_layouts_match_c(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "acp.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(acp_grid), sizeof(acp_kernel),"
+        " sizeof(acp_atoms), sizeof(acp_options), sizeof(acp_stats), offsetof(acp_options, sketch),"
+        " offsetof(acp_options, deadline_s), offsetof(acp_stats, asymmetry)); return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    py = [ctypes.sizeof(B.Grid), ctypes.sizeof(B.Kernel), ctypes.sizeof(B.Atoms), ctypes.sizeof(B.Options),
+          ctypes.sizeof(B.Stats), B.Options.sketch.offset, B.Options.deadline_s.offset, B.Stats.asymmetry.offset]
+    assert out == py
+
+
+def test_null_arguments_are_rejected_without_a_gpu(lib):
+    out = ctypes.c_void_p()
+    assert lib.acp_init(ctypes.byref(out), None, None, None, None, None, 0, None, None) == 1
+    assert lib.acp_apply_chi0(None, None, 0, None, None) == 1
