@@ -134,6 +134,17 @@ def config(index: int) -> System:
     raise ValueError(f"configuration {index} is not available")
 
 
+def mixed_chain(n_atoms: int, n_grid: int, seed: int = 0, scale: float = 0.5) -> System:
+    """Config-2 recipe at another size: atoms every 10 bohr with uniform +-0.5 displacements,
+    Z uniform in {1, 2}, sigma 1, kappa 0.01, occupation 1 (for mid-size profiling runs)."""
+    rng = _rng(50, seed)
+    disp = rng.uniform(-0.5, 0.5, n_atoms)
+    Z = rng.integers(1, 3, n_atoms).astype(np.float64)
+    R = ((np.arange(n_atoms) + 0.5) * 10.0 + disp).reshape(n_atoms, 1)
+    return System(name=f"chain{n_atoms}_mixed_s{seed}", dim=1, n=(int(n_grid),), L=(10.0 * n_atoms,), R=R, Z=Z,
+                  sigma=np.ones(n_atoms), mass=np.ones(n_atoms), kappa=0.01, scale=scale, occ=1)
+
+
 def small_chain(n_atoms=4, n_grid=160, seed=0, mixed=True, displacement=0.3, spacing=10.0, occ=1,
                 scale=1.0) -> System:
     """Small random chains for parity tests (several tiles and a ragged tail at small sizes)."""

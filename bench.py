@@ -31,10 +31,13 @@ sys.path.insert(0, ROOT)
 METRIC = "Sternheimer RHS solved/s and dynamical-matrix time, ACP forms vs plain FP64, 1 GB300"
 UNIT = "RHS/s"
 CONFIG = 2
-ACP_PARAMS = dict(id_tol=1e-8, n_cheb=16, sketch_r=8, dyson_tol=1e-9, dyson_maxit=20, stern_tol=1e-11)
+ACP_PARAMS = dict(id_tol=1e-8, n_cheb=16, sketch_r=8, dyson_tol=1e-6, dyson_maxit=20, stern_tol=1e-11)
 
 
 def workload_name():
+    if WORKLOAD == "chain64":
+        return ("1D periodic rHF chain, 64 atoms (config-2 recipe at half size, N=2560) for profiler captures; "
+                f"ACP FP64 (N_c={ACP_PARAMS['n_cheb']}, id_tol={ACP_PARAMS['id_tol']:g})")
     return ("1D periodic rHF chain, 128 atoms spaced 10 bohr with +-0.5 displacements, Z in {1,2}, sigma 1, "
             "kappa 0.01, kernel scale 0.5, N=5120, 192 occupied orbitals, 128 perturbations; ACP FP64 "
             f"(N_c={ACP_PARAMS['n_cheb']}, id_tol={ACP_PARAMS['id_tol']:g}, SRFT r={ACP_PARAMS['sketch_r']}, "
@@ -140,10 +143,15 @@ def barrier(dist):
 
 
 # ---- the GPU arm -------------------------------------------------------------------------------
+WORKLOAD = "c2"
+
+
 def build_inputs():
-    import numpy as np
     import acp_workloads as W
-    s = W.config(CONFIG)
+    if WORKLOAD == "chain64":
+        s = W.mixed_chain(64, 2560, seed=0)
+    else:
+        s = W.config(CONFIG)
     gs = W.ground_state(s)
     om = W.srft_sketch(s.n_pert, ACP_PARAMS["sketch_r"], CONFIG)
     return s, gs, om
@@ -353,7 +361,11 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["acp", "reference"], default="acp")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["c2", "chain64"], default="c2",
+                    help="c2: the benchmark configuration; chain64: half-size chain for profiler captures")
     args = ap.parse_args(argv)
+    global WORKLOAD
+    WORKLOAD = args.workload
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -80,3 +80,22 @@ def chi0_matrix_sos(model, spectrum=None):
         P = Phi[:, i:i + 1] * Phi[:, no:]
         C += (P / (w[i] - w[no:])) @ P.T
     return 2.0 * model.f * C
+
+
+def chi0_apply_sos(model, G, spectrum=None):
+    """chi0 G from Eq. AdlerWiser without forming the N x N matrix (large grids, few columns).
+
+    For each column g: chi0 g = 2f sum_i psi_i * [sum_{a > N_e} phi_a (phi_a . (psi_i g) h) / (eps_i - eps_a)].
+    """
+    w, Phi = full_spectrum(model) if spectrum is None else spectrum
+    no = model.n_orb
+    Pu, wu = Phi[:, no:], w[no:]
+    Po, wo = Phi[:, :no], w[:no]
+    G = np.asarray(G, dtype=np.float64)
+    out = np.zeros_like(G)
+    for j in range(G.shape[1]):
+        M = Po * G[:, j:j + 1]                      # psi_i * g, (N, N_e)
+        T = (Pu.T @ M) * model.h                    # (N_u, N_e)
+        T /= (wo[None, :] - wu[:, None])
+        out[:, j] = 2.0 * model.f * np.sum(Po * (Pu @ T), axis=1)
+    return out

@@ -49,7 +49,8 @@ class Options(ctypes.Structure):
     _fields_ = [("method", c_int), ("occ", c_double), ("n_cheb", c_int), ("id_tol", c_double),
                 ("sketch_cols", c_int), ("sketch", POINTER(c_double)), ("max_rank", c_int),
                 ("stern_tol", c_double), ("stern_maxit", c_int), ("dyson_tol", c_double),
-                ("dyson_maxit", c_int), ("rhs_batch", c_int), ("deadline_s", c_double)]
+                ("dyson_maxit", c_int), ("rhs_batch", c_int), ("deadline_s", c_double),
+                ("project_every", c_int), ("ms_variant", c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -128,11 +129,12 @@ def _check_block(t, N, name):
 
 def options(method=ACP_METHOD_ACP, occ=1.0, n_cheb=16, id_tol=1e-5, sketch=None, max_rank=0,
             stern_tol=1e-11, stern_maxit=5000, dyson_tol=1e-10, dyson_maxit=30, rhs_batch=0,
-            deadline_s=0.0):
+            deadline_s=0.0, project_every=0, ms_variant=0):
     """Options as a dict (the sketch Omega, if given, is an (n_cols, r) float64 array)."""
     return dict(method=method, occ=occ, n_cheb=n_cheb, id_tol=id_tol, sketch=sketch, max_rank=max_rank,
                 stern_tol=stern_tol, stern_maxit=stern_maxit, dyson_tol=dyson_tol, dyson_maxit=dyson_maxit,
-                rhs_batch=rhs_batch, deadline_s=deadline_s)
+                rhs_batch=rhs_batch, deadline_s=deadline_s, project_every=project_every,
+                ms_variant=ms_variant)
 
 
 class Context:
@@ -188,6 +190,8 @@ class Context:
         o.dyson_maxit = int(d["dyson_maxit"])
         o.rhs_batch = int(d["rhs_batch"])
         o.deadline_s = float(d["deadline_s"])
+        o.project_every = int(d.get("project_every", 0))
+        o.ms_variant = int(d.get("ms_variant", 0))
         self._opts = o
         return o
 

@@ -121,6 +121,8 @@ acp_status validate_options(acp_ctx* ctx, const acp_options* o) {
   if (!(o->stern_tol > 0) || o->stern_maxit < 1) return set_error(ctx, ACP_E_ARG, "bad Sternheimer tolerance/maxit");
   if (!(o->dyson_tol > 0)) return set_error(ctx, ACP_E_ARG, "bad Dyson tolerance");
   if (o->sketch_cols < 0) return set_error(ctx, ACP_E_ARG, "negative sketch_cols");
+  if (o->project_every < 0) return set_error(ctx, ACP_E_ARG, "negative project_every");
+  if (o->ms_variant < 0 || o->ms_variant > 2) return set_error(ctx, ACP_E_ARG, "ms_variant must be 0, 1 or 2");
   return ACP_OK;
 }
 

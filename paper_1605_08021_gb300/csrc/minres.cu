@@ -272,6 +272,163 @@ __global__ void __launch_bounds__(kThreads) ms_step_kernel(int N, int nmu, int n
   }
 }
 
+// ---- multi-shift MINRES with a stored Lanczos basis -----------------------------------------
+// Instead of carrying w_{k-1}, w_{k-2} and x for every shift (6 vector passes per shift and
+// step), the normalised Lanczos vectors v_1..v_k of each mu are kept, together with the per-step
+// coefficients of every shift's Givens factorisation R (diagonal gamma_j, first superdiagonal
+// delta_{j+1}, second eps_{j+2}) and phi_j.  MINRES's iterate is x_c = V R_c^{-1} phi_c, so at the
+// end y_c = R_c^{-1} phi_c is a banded back substitution and X_mu = V_mu Y_mu one small GEMM.
+struct MsBasis {
+  double* Vb;        // slot s of mu at Vb + mu * slot_ld + s * N; slot 0 = v_0 = 0
+  size_t slot_ld;    // (kmax + 2) * N
+  double* P;         // N x nmu, the unnormalised next Lanczos vector
+  double *alpha, *beta, *beta1;             // nmu
+  double *cs, *sn, *dbar, *epsln, *phibar;  // nc x nmu (c + nc mu)
+  double* coef;      // (gamma, delta, eps, phi) of step j: coef[(((size_t)mu * nc + c) * kmax + j) * 4 + q]
+  double* Y;         // y_{c, j}: Y[((size_t)mu * nc + c) * kmax + j]
+  int *active, *iters;
+  const double* nodes;
+  int kmax;
+};
+
+__global__ void __launch_bounds__(kThreads) msb_init_kernel(int N, int nmu, int nc, const double* __restrict__ Bm,
+                                                            MsBasis s, int* nan_flag) {
+  __shared__ double red[32];
+  const int mu = blockIdx.x;
+  const double* b = Bm + (size_t)mu * N;
+  double acc = 0.0;
+  for (int a = threadIdx.x; a < N; a += blockDim.x) acc += b[a] * b[a];
+  const double nrm = sqrt(block_sum(acc, red));
+  const bool ok = isfinite(nrm) && nrm > 0.0;
+  const double inv = ok ? 1.0 / nrm : 0.0;
+  double* v0 = s.Vb + (size_t)mu * s.slot_ld;
+  for (int a = threadIdx.x; a < N; a += blockDim.x) {
+    v0[a] = 0.0;
+    v0[N + a] = b[a] * inv;
+  }
+  if (threadIdx.x < nc) {
+    const int q = threadIdx.x + nc * mu;
+    s.cs[q] = -1.0;
+    s.sn[q] = 0.0;
+    s.dbar[q] = 0.0;
+    s.epsln[q] = 0.0;
+    s.phibar[q] = ok ? nrm : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    s.beta1[mu] = ok ? nrm : 0.0;
+    s.beta[mu] = 0.0;
+    s.iters[mu] = 0;
+    s.active[mu] = ok ? 1 : 0;
+    if (!isfinite(nrm)) atomicExch(nan_flag, 1);
+  }
+}
+
+// Step k (1-based): P = Q[H v_k - alpha v_k - beta_k v_{k-1}] is given; store v_{k+1} = P/||P|| in
+// slot k+1 and advance every shift's Givens factorisation.
+__global__ void __launch_bounds__(kThreads) msb_step_kernel(int N, int nmu, int nc, int k, MsBasis s, double tol,
+                                                            int* nan_flag) {
+  __shared__ double red[32];
+  __shared__ int any_active;
+  const int mu = blockIdx.x;
+  if (!s.active[mu]) return;
+  const double* P = s.P + (size_t)mu * N;
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < N; r += blockDim.x) acc += P[r] * P[r];
+  const double bn = sqrt(block_sum(acc, red));
+  const double ib = (bn > 0.0) ? 1.0 / bn : 0.0;
+  double* vn = s.Vb + (size_t)mu * s.slot_ld + (size_t)(k + 1) * N;
+  for (int r = threadIdx.x; r < N; r += blockDim.x) vn[r] = P[r] * ib;
+  if (threadIdx.x == 0) any_active = 0;
+  __syncthreads();
+  const double a = s.alpha[mu];
+  if (threadIdx.x < nc) {
+    const int c = threadIdx.x;
+    const int q = c + nc * mu;
+    const double ac = a - s.nodes[c];
+    const double cs = s.cs[q], sg = s.sn[q], db = s.dbar[q], pb = s.phibar[q], oldeps = s.epsln[q];
+    const double delta = cs * db + sg * ac;
+    const double gbar = sg * db - cs * ac;
+    const double gamma = fmax(hypot(gbar, bn), 1e-300);
+    const double cn = gbar / gamma, sn_ = bn / gamma;
+    const double phi = cn * pb, pbn = sn_ * pb;
+    double* cf = s.coef + (((size_t)mu * nc + c) * s.kmax + (k - 1)) * 4;
+    cf[0] = gamma;
+    cf[1] = delta;
+    cf[2] = oldeps;
+    cf[3] = phi;
+    s.epsln[q] = sg * bn;
+    s.dbar[q] = -cs * bn;
+    s.cs[q] = cn;
+    s.sn[q] = sn_;
+    s.phibar[q] = pbn;
+    if (!isfinite(pbn)) atomicExch(nan_flag, 1);
+    if (isfinite(pbn) && !(fabs(pbn) <= tol * s.beta1[mu])) atomicOr(&any_active, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s.beta[mu] = bn;
+    const int it = s.iters[mu] + 1;
+    s.iters[mu] = it;
+    if (!isfinite(bn)) atomicExch(nan_flag, 1);
+    if (!any_active || !isfinite(bn) || bn == 0.0 || it >= s.kmax) s.active[mu] = 0;
+  }
+}
+
+// y_c = R_c^{-1} phi_c, one thread per (mu, c): y_j = (phi_j - delta_{j+1} y_{j+1} - eps_{j+2} y_{j+2}) / gamma_j
+__global__ void msb_backsub_kernel(int nmu, int nc, MsBasis s) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)nmu * nc) return;
+  const int mu = (int)(t / nc);
+  const int kk = s.iters[mu];
+  const double* cf = s.coef + t * s.kmax * 4;
+  double* y = s.Y + t * s.kmax;
+  double y1 = 0.0, y2 = 0.0;  // y_{j+1}, y_{j+2}
+  for (int j = kk - 1; j >= 0; --j) {
+    const double d1 = (j + 1 < kk) ? cf[(j + 1) * 4 + 1] : 0.0;
+    const double e2 = (j + 2 < kk) ? cf[(j + 2) * 4 + 2] : 0.0;
+    const double yj = (cf[j * 4 + 3] - d1 * y1 - e2 * y2) / cf[j * 4 + 0];
+    y[j] = yj;
+    y2 = y1;
+    y1 = yj;
+  }
+}
+
+// X[:, mu + c nmu] = sum_j v_{j+1} y_{c, j}: grid (row tiles, mu); 16 shifts per pass.
+__global__ void __launch_bounds__(256) msb_assemble_kernel(int N, int nmu, int nc, MsBasis s, double* __restrict__ X) {
+  __shared__ double ys[64][16];
+  const int mu = blockIdx.y;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int kk = s.iters[mu];
+  const double* V = s.Vb + (size_t)mu * s.slot_ld + N;  // v_1 in slot 1
+  for (int c0 = 0; c0 < nc; c0 += 16) {
+    const int cw = (nc - c0 < 16) ? nc - c0 : 16;
+    double acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+    for (int j0 = 0; j0 < kk; j0 += 64) {
+      const int jw = (kk - j0 < 64) ? kk - j0 : 64;
+      __syncthreads();
+      for (int e = threadIdx.x; e < 64 * 16; e += blockDim.x) {
+        const int j = e / 16, c = e % 16;
+        ys[j][c] = (j < jw && c < cw) ? s.Y[((size_t)mu * nc + c0 + c) * s.kmax + j0 + j] : 0.0;
+      }
+      __syncthreads();
+      if (r < N) {
+        for (int j = 0; j < jw; ++j) {
+          const double v = V[(size_t)(j0 + j) * N + r];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc[c] = fma(v, ys[j][c], acc[c]);
+        }
+      }
+    }
+    if (r < N) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (c < cw) X[((size_t)mu + (size_t)(c0 + c) * nmu) * N + r] = acc[c];
+    }
+  }
+}
+
 acp_status count_active(acp_ctx* ctx, const int* active, int n, int* out_h) {
   int* cnt = ctx->d_flag + 4;
   ACP_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(int), ctx->stream));
@@ -324,6 +481,28 @@ acp_status collect_report(acp_ctx* ctx, int n, const int* iters, const double* p
 
 }  // namespace
 
+// Projection period of the Lanczos vectors.  Rounding puts occupied components of relative size
+// ~1e-14 into each new vector (H v is exact in the unoccupied space only up to rounding and the
+// eigenvector residual).  Between projections they are multiplied by Lanczos polynomials of the
+// unoccupied spectrum [eps_{N+1}, E_max] evaluated at an occupied eigenvalue at distance d below
+// it, which grow at most like rho^k, rho = x + sqrt(x^2 - 1), x = 1 + 2 d / (E_max - eps_{N+1})
+// (Chebyshev bound).  d <= eps_N - eps_1 + 1 is assumed (gap below 1 Ha), E_max >= the largest
+// kinetic energy; the period keeps rho^m <= 100.
+int projection_period(const acp_ctx* ctx) {
+  if (ctx->opt.project_every > 0) return ctx->opt.project_every;
+  const double kmax = M_PI * ctx->N / ctx->L;
+  const double emax = 0.5 * kmax * kmax;
+  const double d = ctx->eps.back() - ctx->eps.front() + 1.0;
+  const double span = emax - ctx->eps.back();
+  if (!(span > 0)) return 1;
+  const double x = 1.0 + 2.0 * d / span;
+  const double rho = x + sqrt(x * x - 1.0);
+  int m = (int)floor(log(100.0) / log(rho));
+  if (m < 1) m = 1;
+  if (m > 32) m = 32;
+  return m;
+}
+
 acp_status minres_batched(acp_ctx* ctx, const double* B, int ncol, const double* shift_d, double* X,
                           SolveReport* rep, double t0_ms) {
   if (ncol <= 0) return ACP_OK;
@@ -346,9 +525,10 @@ acp_status minres_batched(acp_ctx* ctx, const double* B, int ncol, const double*
   ACP_LAUNCH(ctx);
   const double tol = ctx->opt.stern_tol;
   const int maxit = ctx->opt.stern_maxit;
+  const int period = projection_period(ctx);
   for (int it = 0; it < maxit; ++it) {
     ACP_TRY(spectral_apply(ctx, s.V, N, ncol, MULT_KINETIC, true, shift_d, s.P, N, s.alpha, s.active, s.Vp, s.beta));
-    ACP_TRY(project(ctx, s.P, N, ncol, s.P, N));
+    if (it % period == period - 1 || it < 2) ACP_TRY(project(ctx, s.P, N, ncol, s.P, N));
     ::acp::note_launch(ctx);
     minres_step_kernel<<<ncol, kThreads, 0, ctx->stream>>>(N, s, X, tol, maxit, ctx->d_flag);
     ACP_LAUNCH(ctx);
@@ -364,8 +544,8 @@ acp_status minres_batched(acp_ctx* ctx, const double* B, int ncol, const double*
   return ACP_OK;
 }
 
-acp_status minres_multishift(acp_ctx* ctx, const double* B, int nmu, const double* nodes_d, int nc, double* X,
-                             SolveReport* rep, double t0_ms) {
+static acp_status minres_multishift_vectors(acp_ctx* ctx, const double* B, int nmu, const double* nodes_d, int nc,
+                                            double* X, SolveReport* rep, double t0_ms) {
   if (nmu <= 0) return ACP_OK;
   if (nc < 1 || nc > kMaxShifts) return set_error(ctx, ACP_E_ARG, "number of shifts %d outside [1, %d]", nc, kMaxShifts);
   const int N = ctx->N;
@@ -390,9 +570,10 @@ acp_status minres_multishift(acp_ctx* ctx, const double* B, int nmu, const doubl
   ACP_LAUNCH(ctx);
   const double tol = ctx->opt.stern_tol;
   const int maxit = ctx->opt.stern_maxit;
+  const int period = projection_period(ctx);
   for (int it = 0; it < maxit; ++it) {
     ACP_TRY(spectral_apply(ctx, s.V, N, nmu, MULT_KINETIC, true, nullptr, s.P, N, s.alpha, s.active, s.Vp, s.beta));
-    ACP_TRY(project(ctx, s.P, N, nmu, s.P, N));
+    if (it % period == period - 1 || it < 2) ACP_TRY(project(ctx, s.P, N, nmu, s.P, N));
     ::acp::note_launch(ctx);
     ms_step_kernel<<<nmu, kThreads, 0, ctx->stream>>>(N, nmu, nc, s, X, tol, maxit, ctx->d_flag);
     ACP_LAUNCH(ctx);
@@ -423,6 +604,107 @@ acp_status minres_multishift(acp_ctx* ctx, const double* B, int nmu, const doubl
   if (h.max_res > rep->max_rel_res) rep->max_rel_res = h.max_res;
   if ((long long)h.conv < (long long)nq) rep->all_converged = false;
   return ACP_OK;
+}
+
+
+static acp_status ms_report(acp_ctx* ctx, int nmu, int nc, const int* iters, const double* phibar, const double* beta1,
+                            double tol, SolveReport* rep) {
+  const size_t nq = (size_t)nc * nmu;
+  Report* d = nullptr;
+  ACP_TRY(ws(ctx, "minres_report", 1, &d));
+  ACP_CUDA(ctx, cudaMemsetAsync(d, 0, sizeof(Report), ctx->stream));
+  int blocks = (int)((nq + 255) / 256);
+  if (blocks > 1024) blocks = 1024;
+  ::acp::note_launch(ctx);
+  ms_report_kernel<<<blocks, 256, 0, ctx->stream>>>(nmu, nc, iters, phibar, beta1, tol, &d->steps, &d->max_it,
+                                                    &d->conv, &d->max_res);
+  ACP_LAUNCH(ctx);
+  Report h{};
+  ACP_CUDA(ctx, cudaMemcpyAsync(&h, d, sizeof(Report), cudaMemcpyDeviceToHost, ctx->stream));
+  ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  rep->steps += (long long)h.steps;
+  rep->converged += (long long)h.conv;
+  if (h.max_it > rep->max_iters) rep->max_iters = h.max_it;
+  if (h.max_res > rep->max_rel_res) rep->max_rel_res = h.max_res;
+  if ((long long)h.conv < (long long)nq) rep->all_converged = false;
+  return ACP_OK;
+}
+
+static acp_status minres_multishift_basis(acp_ctx* ctx, const double* B, int nmu, const double* nodes_d, int nc,
+                                          double* X, int kmax, SolveReport* rep, double t0_ms) {
+  const int N = ctx->N;
+  MsBasis s{};
+  s.kmax = kmax;
+  s.slot_ld = (size_t)(kmax + 2) * N;
+  double *vb = nullptr, *sc = nullptr, *cf = nullptr, *yb = nullptr, *pb = nullptr;
+  int* iv = nullptr;
+  const size_t nq = (size_t)nc * nmu;
+  ACP_TRY(ws(ctx, "msb_basis", s.slot_ld * nmu, &vb));
+  ACP_TRY(ws(ctx, "msb_p", (size_t)N * nmu, &pb));
+  ACP_TRY(ws(ctx, "msb_sc", 3 * (size_t)nmu + 5 * nq, &sc));
+  ACP_TRY(ws(ctx, "msb_coef", 4 * nq * kmax, &cf));
+  ACP_TRY(ws(ctx, "msb_y", nq * kmax, &yb));
+  ACP_TRY(ws(ctx, "msb_iv", 2 * (size_t)nmu, &iv));
+  s.Vb = vb; s.P = pb; s.coef = cf; s.Y = yb;
+  s.alpha = sc; s.beta = sc + nmu; s.beta1 = sc + 2 * nmu;
+  double* q = sc + 3 * nmu;
+  s.cs = q; s.sn = q + nq; s.dbar = q + 2 * nq; s.epsln = q + 3 * nq; s.phibar = q + 4 * nq;
+  s.active = iv; s.iters = iv + nmu;
+  s.nodes = nodes_d;
+  ACP_CUDA(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+  ::acp::note_launch(ctx);
+  msb_init_kernel<<<nmu, kThreads, 0, ctx->stream>>>(N, nmu, nc, B, s, ctx->d_flag);
+  ACP_LAUNCH(ctx);
+  const double tol = ctx->opt.stern_tol;
+  const int period = projection_period(ctx);
+  int k = 1;
+  for (; k <= kmax; ++k) {
+    const double* vk = s.Vb + (size_t)k * N;
+    const double* vkm = s.Vb + (size_t)(k - 1) * N;
+    ACP_TRY(spectral_apply(ctx, vk, (int)s.slot_ld, nmu, MULT_KINETIC, true, nullptr, s.P, N, s.alpha, s.active, vkm,
+                           s.beta));
+    if ((k - 1) % period == period - 1 || k <= 2) ACP_TRY(project(ctx, s.P, N, nmu, s.P, N));
+    ::acp::note_launch(ctx);
+    msb_step_kernel<<<nmu, kThreads, 0, ctx->stream>>>(N, nmu, nc, k, s, tol, ctx->d_flag);
+    ACP_LAUNCH(ctx);
+    if ((k & 15) == 0 || k == kmax) {
+      int n_act = 0;
+      ACP_TRY(count_active(ctx, s.active, nmu, &n_act));
+      if (n_act == 0) break;
+      if (deadline_passed(ctx, t0_ms)) return set_error(ctx, ACP_E_TIMEOUT, "deadline passed in MINRES");
+    }
+  }
+  ACP_TRY(check_nan(ctx));
+  ::acp::note_launch(ctx);
+  msb_backsub_kernel<<<(int)((nq + 127) / 128), 128, 0, ctx->stream>>>(nmu, nc, s);
+  ACP_LAUNCH(ctx);
+  ::acp::note_launch(ctx);
+  msb_assemble_kernel<<<dim3((N + 255) / 256, nmu), 256, 0, ctx->stream>>>(N, nmu, nc, s, X);
+  ACP_LAUNCH(ctx);
+  return ms_report(ctx, nmu, nc, s.iters, s.phibar, s.beta1, tol, rep);
+}
+
+acp_status minres_multishift(acp_ctx* ctx, const double* B, int nmu, const double* nodes_d, int nc, double* X,
+                             SolveReport* rep, double t0_ms) {
+  if (nmu <= 0) return ACP_OK;
+  if (nc < 1 || nc > kMaxShifts) return set_error(ctx, ACP_E_ARG, "number of shifts %d outside [1, %d]", nc, kMaxShifts);
+  if (ctx->opt.ms_variant != 2) {
+    // stored-basis variant: up to 512 Lanczos steps, within min(32 GB, half the free memory)
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    auto it = ctx->ws.bufs.find("msb_basis");  // memory this buffer already holds counts as available
+    if (it != ctx->ws.bufs.end()) free_b += it->second.second;
+    size_t budget = free_b / 2;
+    if (budget > (size_t(32) << 30)) budget = size_t(32) << 30;
+    const size_t per_slot = (size_t)ctx->N * nmu * sizeof(double) + (size_t)nc * nmu * 5 * sizeof(double);
+    const size_t fit = per_slot ? budget / per_slot : 0;
+    int kmax = ctx->opt.stern_maxit;
+    if (kmax > 512) kmax = 512;
+    if ((size_t)kmax + 2 > fit) kmax = (int)fit - 2;
+    if (kmax >= 64 || ctx->opt.ms_variant == 1)
+      return minres_multishift_basis(ctx, B, nmu, nodes_d, nc, X, kmax < 1 ? 1 : kmax, rep, t0_ms);
+  }
+  return minres_multishift_vectors(ctx, B, nmu, nodes_d, nc, X, rep, t0_ms);
 }
 
 }  // namespace acp

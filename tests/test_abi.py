@@ -41,12 +41,12 @@ def test_struct_layouts_match_c(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "acp.h"\n'
         "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(acp_grid), sizeof(acp_kernel),"
         " sizeof(acp_atoms), sizeof(acp_options), sizeof(acp_stats), offsetof(acp_options, sketch),"
-        " offsetof(acp_options, deadline_s), offsetof(acp_stats, asymmetry)); return 0;}\n")
+        " offsetof(acp_options, project_every), offsetof(acp_stats, asymmetry)); return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     py = [ctypes.sizeof(B.Grid), ctypes.sizeof(B.Kernel), ctypes.sizeof(B.Atoms), ctypes.sizeof(B.Options),
-          ctypes.sizeof(B.Stats), B.Options.sketch.offset, B.Options.deadline_s.offset, B.Stats.asymmetry.offset]
+          ctypes.sizeof(B.Stats), B.Options.sketch.offset, B.Options.project_every.offset, B.Stats.asymmetry.offset]
     assert out == py
 
 
