@@ -157,10 +157,14 @@ def build_inputs():
     return s, gs, om
 
 
+PRECISION = 0
+
+
 def make_context(P, s, gs, om, V, psi):
     o = P.options(method=P.ACP_METHOD_ACP, occ=float(s.occ), sketch=om, id_tol=ACP_PARAMS["id_tol"],
                   n_cheb=ACP_PARAMS["n_cheb"], dyson_tol=ACP_PARAMS["dyson_tol"],
-                  dyson_maxit=ACP_PARAMS["dyson_maxit"], stern_tol=ACP_PARAMS["stern_tol"])
+                  dyson_maxit=ACP_PARAMS["dyson_maxit"], stern_tol=ACP_PARAMS["stern_tol"],
+                  precision=PRECISION)
     return P.Context(s.n[0], s.L[0], s.kappa, s.scale, V, psi, gs.eps[: gs.n_orb], o)
 
 
@@ -211,7 +215,7 @@ def run_gpu(args):
     barrier(dist)
     launches = ctx.launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
-    prof = {k: ctx.profile_get(k) for k in ("dgemm", "spectral")}
+    prof = {k: ctx.profile_get(k) for k in ("dgemm", "spectral", "spectral32", "tc_gemm")}
     ctx.profile(False)
     clk = clocks.stop()
 
@@ -253,21 +257,33 @@ def run_gpu(args):
         roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": None, "kernel": "dgemm_kernel (FP64 projector/W GEMMs)",
                 "peak_source": "FP64 DFMA rate from the GB300 unit count and max clock (recipe nominal 1.25 TFLOP/s)"}
+    elif dom == "tc_gemm":
+        achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12 if p["ms"] > 0 else 0.0
+        # TF32 dense: the measured bf16 burst peak x the nominal TF32/BF16 ratio (1.1 / 2.25)
+        peak = float(peaks["bf16_tflops"]) * 1.1 / 2.25
+        roof = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "tc3_gemm_kernel (projector, tcgen05 3xTF32; algorithmic 2MNK flops, 3 MMA passes)",
+                "peak_source": f"bf16_tflops of {peak_src} x 1.1/2.25 (nominal TF32/BF16)"}
     else:
         achieved = p["bytes"] / (p["ms"] * 1e-3) / 1e9 if p["ms"] > 0 else 0.0
         peak = float(peaks["hbm_gbs"])
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "kernel": "spectral_kernel",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": dom + "_kernel",
                 "peak_source": f"hbm_gbs of {peak_src}"}
+    roof["kernel_ms"] = {k: round(v["ms"], 2) for k, v in prof.items()}
     roof["share_of_step"] = round(p["ms"] / ms, 4) if ms > 0 else None
     roof["launches"] = p["launches"]
     st = stats[-1]
     line = {
         "metric": METRIC, "value": round(pairs_all / (ms_max * 1e-3), 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if PRECISION == 0 else "f32+tf32x3/f64", "data": "synthetic",
         "config": {"workload": workload_name(), "l2": "working set (Krylov state, ~GB) larger than L2",
-                   "parallelism": f"replicas x{world}", "method": "ACP (Alg. 2 Remark + Alg. 3 + Alg. 4), FP64"},
+                   "parallelism": f"replicas x{world}",
+                   "method": "ACP (Alg. 2 Remark + Alg. 3 + Alg. 4), " + ("FP64" if PRECISION == 0 else
+                             "mixed: FP32 MINRES + 3xTF32 tcgen05 projector + FP64 refinement")},
         "rhs_pairs_per_step": pairs / args.steps, "n_mu": st["n_mu"], "alg4_iters": st["outer_iters"],
         "solve_ms_per_step": round(sum(x["ms_solve"] for x in stats) / len(stats), 2),
         "compress_ms_per_step": round(sum(x["ms_compress"] for x in stats) / len(stats), 2),
@@ -363,9 +379,12 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["c2", "chain64"], default="c2",
                     help="c2: the benchmark configuration; chain64: half-size chain for profiler captures")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="arithmetic of the Sternheimer solves")
     args = ap.parse_args(argv)
-    global WORKLOAD
+    global WORKLOAD, PRECISION
     WORKLOAD = args.workload
+    PRECISION = 1 if args.precision == "mixed" else 0
     if args.impl == "reference":
         run_reference(args)
     else:

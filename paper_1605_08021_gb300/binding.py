@@ -20,6 +20,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "acp.h")
 
 ACP_METHOD_PLAIN = 0
 ACP_METHOD_ACP = 1
+ACP_PREC_FP64 = 0
+ACP_PREC_MIXED = 1
 
 STATUS = {0: "ACP_OK", 1: "ACP_E_ARG", 2: "ACP_E_CUDA", 3: "ACP_E_OOM", 4: "ACP_E_NOCONV",
           5: "ACP_E_TIMEOUT", 6: "ACP_E_GAP", 7: "ACP_E_RANK", 8: "ACP_E_NUMERIC"}
@@ -50,7 +52,7 @@ class Options(ctypes.Structure):
                 ("sketch_cols", c_int), ("sketch", POINTER(c_double)), ("max_rank", c_int),
                 ("stern_tol", c_double), ("stern_maxit", c_int), ("dyson_tol", c_double),
                 ("dyson_maxit", c_int), ("rhs_batch", c_int), ("deadline_s", c_double),
-                ("project_every", c_int), ("ms_variant", c_int)]
+                ("project_every", c_int), ("ms_variant", c_int), ("precision", c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -92,6 +94,7 @@ def load():
         "acp_phonons": (I, [P, D, I, D, D]),
         "acp_hamiltonian_apply": (I, [P, P, I, D, P]),
         "acp_project": (I, [P, P, I, P]),
+        "acp_project_mixed": (I, [P, P, I, P]),
         "acp_kernel_apply": (I, [P, P, I, I, P]),
         "acp_sternheimer_solve": (I, [P, P, I, D, P, POINTER(Stats)]),
         "acp_compress": (I, [P, P, I, I, POINTER(c_int), POINTER(c_int), P, D]),
@@ -129,12 +132,12 @@ def _check_block(t, N, name):
 
 def options(method=ACP_METHOD_ACP, occ=1.0, n_cheb=16, id_tol=1e-5, sketch=None, max_rank=0,
             stern_tol=1e-11, stern_maxit=5000, dyson_tol=1e-10, dyson_maxit=30, rhs_batch=0,
-            deadline_s=0.0, project_every=0, ms_variant=0):
+            deadline_s=0.0, project_every=0, ms_variant=0, precision=0):
     """Options as a dict (the sketch Omega, if given, is an (n_cols, r) float64 array)."""
     return dict(method=method, occ=occ, n_cheb=n_cheb, id_tol=id_tol, sketch=sketch, max_rank=max_rank,
                 stern_tol=stern_tol, stern_maxit=stern_maxit, dyson_tol=dyson_tol, dyson_maxit=dyson_maxit,
                 rhs_batch=rhs_batch, deadline_s=deadline_s, project_every=project_every,
-                ms_variant=ms_variant)
+                ms_variant=ms_variant, precision=precision)
 
 
 class Context:
@@ -192,6 +195,7 @@ class Context:
         o.deadline_s = float(d["deadline_s"])
         o.project_every = int(d.get("project_every", 0))
         o.ms_variant = int(d.get("ms_variant", 0))
+        o.precision = int(d.get("precision", 0))
         self._opts = o
         return o
 
@@ -302,6 +306,12 @@ class Context:
         _check_block(X, self.N, "X")
         Y = self._out(X.shape[0])
         self._call(self.lib.acp_project(self.ptr, _tptr(X), X.shape[0], _tptr(Y)))
+        return Y
+
+    def project_mixed(self, X):
+        _check_block(X, self.N, "X")
+        Y = self._out(X.shape[0])
+        self._call(self.lib.acp_project_mixed(self.ptr, _tptr(X), X.shape[0], _tptr(Y)))
         return Y
 
     def kernel_apply(self, X, inverse=False):

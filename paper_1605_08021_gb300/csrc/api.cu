@@ -123,6 +123,8 @@ acp_status validate_options(acp_ctx* ctx, const acp_options* o) {
   if (o->sketch_cols < 0) return set_error(ctx, ACP_E_ARG, "negative sketch_cols");
   if (o->project_every < 0) return set_error(ctx, ACP_E_ARG, "negative project_every");
   if (o->ms_variant < 0 || o->ms_variant > 2) return set_error(ctx, ACP_E_ARG, "ms_variant must be 0, 1 or 2");
+  if (o->precision != ACP_PREC_FP64 && o->precision != ACP_PREC_MIXED)
+    return set_error(ctx, ACP_E_ARG, "unknown precision %d", o->precision);
   return ACP_OK;
 }
 
@@ -400,6 +402,14 @@ acp_status acp_project(acp_ctx* ctx, const double* X_d, int ncol, double* Y_d) {
   return ACP_OK;
 }
 
+acp_status acp_project_mixed(acp_ctx* ctx, const double* X_d, int ncol, double* Y_d) {
+  ACP_TRY(check_ctx(ctx));
+  if (!X_d || !Y_d || ncol < 0) return set_error(ctx, ACP_E_ARG, "bad arguments");
+  ACP_TRY(project_mixed64(ctx, X_d, ncol, Y_d));
+  ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return ACP_OK;
+}
+
 acp_status acp_kernel_apply(acp_ctx* ctx, const double* X_d, int ncol, int kernel_op, double* Y_d) {
   ACP_TRY(check_ctx(ctx));
   if (!X_d || !Y_d || ncol < 0 || (kernel_op != 1 && kernel_op != -1))
@@ -463,6 +473,8 @@ acp_status acp_update(acp_ctx* ctx, const double* v_eff_d, const double* psi_d, 
                                 ctx->stream));
   ACP_CUDA(ctx, cudaMemcpyAsync(ctx->d_eps, eps_h, n_orb * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  ctx->psi32_stale = true;
+  ctx->tables32_stale = true;
   return ACP_OK;
 }
 

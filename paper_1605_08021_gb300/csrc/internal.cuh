@@ -70,6 +70,15 @@ struct acp_ctx {
   double* d_kvec = nullptr;       // N: k with the Nyquist entry zeroed (odd multipliers)
   double2* d_tw = nullptr;        // N: exp(-2 pi i m / N)
   int* d_flag = nullptr;          // device status word / counters (16 ints)
+  // mixed precision: FP32 blocks use leading dimension ld32 (N rounded up to 32); the orbitals
+  // are kept as TF32 hi + FP32 lo parts in both orientations for the tensor-core projector.
+  int ld32 = 0, no_pad = 0;
+  float* d_psi_hi = nullptr;   // n_orb x ld32 (orbital rows)
+  float* d_psi_lo = nullptr;
+  float* d_psiT_hi = nullptr;  // N x no_pad (grid rows, orbitals contiguous)
+  float* d_psiT_lo = nullptr;
+  bool psi32_stale = true;
+  bool tables32_stale = true;     // FP32 copies of the kinetic symbol, V_eff and twiddles
   acp::FftPlan plan;
   acp::Workspace ws;
   acp::Profiler prof;
@@ -173,6 +182,24 @@ struct Compression {
 };
 acp_status compress(acp_ctx* ctx, const double* G, int ncol, const double* sketch_h, int sketch_cols,
                     double id_tol, int max_rank, Compression* out);
+
+// minres32.cu: the same solves with FP32 MINRES (tensor-core projector) and FP64 iterative
+// refinement; used when opt.precision == ACP_PREC_MIXED.
+acp_status minres_batched_mixed(acp_ctx* ctx, const double* B, int ncol, const double* shift_d, double* X,
+                                SolveReport* rep, double t0_ms);
+acp_status minres_multishift_mixed(acp_ctx* ctx, const double* B, int nmu, const double* nodes_d, int nc, double* X,
+                                   SolveReport* rep, double t0_ms);
+// spectral32.cu: FP32 (H - s) X, or the Lanczos form when Xprev is given (see spectral_apply).
+acp_status spectral32_apply(acp_ctx* ctx, const float* X, int ldx, int ncol, const float* shift_d, float* Y, int ldy,
+                            float* alpha_d, const int* active_d, const float* Xprev, int ldp, const float* beta_d);
+
+// tc_gemm.cu: FP32 projector Y = Q X on the tensor cores (3xTF32 tcgen05 GEMMs); X, Y FP32 blocks
+// with leading dimensions that are multiples of 4 (Y may alias X).  mixed_prepare builds the FP32
+// orbital copies when the orbitals changed; tc_check reads the tensor-core status word.
+acp_status mixed_prepare(acp_ctx* ctx);
+acp_status project32(acp_ctx* ctx, const float* X, int ldx, int ncol, float* Y, int ldy);
+acp_status tc_check(acp_ctx* ctx);
+acp_status project_mixed64(acp_ctx* ctx, const double* X, int ncol, double* Y);
 
 // dense.cu: LU solve of an n x n system with nrhs right-hand sides (A, B overwritten; X in B).
 acp_status lu_solve(acp_ctx* ctx, double* A, int n, double* B, int nrhs);

@@ -481,31 +481,22 @@ acp_status collect_report(acp_ctx* ctx, int n, const int* iters, const double* p
 
 }  // namespace
 
-// Projection period of the Lanczos vectors.  Rounding puts occupied components of relative size
-// ~1e-14 into each new vector (H v is exact in the unoccupied space only up to rounding and the
-// eigenvector residual).  Between projections they are multiplied by Lanczos polynomials of the
-// unoccupied spectrum [eps_{N+1}, E_max] evaluated at an occupied eigenvalue at distance d below
-// it, which grow at most like rho^k, rho = x + sqrt(x^2 - 1), x = 1 + 2 d / (E_max - eps_{N+1})
-// (Chebyshev bound).  d <= eps_N - eps_1 + 1 is assumed (gap below 1 Ha), E_max >= the largest
-// kinetic energy; the period keeps rho^m <= 100.
+// Projection period of the Lanczos vectors.  Rounding puts occupied components into each new
+// vector; the shifts of Alg. 1 (eps_i) and of Eq. eqncompressU (Chebyshev nodes) lie inside the
+// occupied band, where H - s has eigenvalues eps_j - s close to zero (the orbitals of distant,
+// nearly isolated atoms are almost degenerate).  Left in the Lanczos basis for a few steps, those
+// components make MINRES resolve the near-zero eigenvalues and its residual stalls (on the
+// 128-atom chain at 1e-8 with a period of 15, while projecting every step converges in ~220
+// steps).  The automatic period is therefore 1; a caller may ask for a longer one.
 int projection_period(const acp_ctx* ctx) {
   if (ctx->opt.project_every > 0) return ctx->opt.project_every;
-  const double kmax = M_PI * ctx->N / ctx->L;
-  const double emax = 0.5 * kmax * kmax;
-  const double d = ctx->eps.back() - ctx->eps.front() + 1.0;
-  const double span = emax - ctx->eps.back();
-  if (!(span > 0)) return 1;
-  const double x = 1.0 + 2.0 * d / span;
-  const double rho = x + sqrt(x * x - 1.0);
-  int m = (int)floor(log(100.0) / log(rho));
-  if (m < 1) m = 1;
-  if (m > 32) m = 32;
-  return m;
+  return 1;
 }
 
 acp_status minres_batched(acp_ctx* ctx, const double* B, int ncol, const double* shift_d, double* X,
                           SolveReport* rep, double t0_ms) {
   if (ncol <= 0) return ACP_OK;
+  if (ctx->opt.precision == ACP_PREC_MIXED) return minres_batched_mixed(ctx, B, ncol, shift_d, X, rep, t0_ms);
   const int N = ctx->N;
   const size_t nv = (size_t)N * ncol;
   MinresState s{};
@@ -688,6 +679,7 @@ acp_status minres_multishift(acp_ctx* ctx, const double* B, int nmu, const doubl
                              SolveReport* rep, double t0_ms) {
   if (nmu <= 0) return ACP_OK;
   if (nc < 1 || nc > kMaxShifts) return set_error(ctx, ACP_E_ARG, "number of shifts %d outside [1, %d]", nc, kMaxShifts);
+  if (ctx->opt.precision == ACP_PREC_MIXED) return minres_multishift_mixed(ctx, B, nmu, nodes_d, nc, X, rep, t0_ms);
   if (ctx->opt.ms_variant != 2) {
     // stored-basis variant: up to 512 Lanczos steps, within min(32 GB, half the free memory)
     size_t free_b = 0, total_b = 0;

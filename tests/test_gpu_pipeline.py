@@ -133,21 +133,6 @@ def test_error_statuses():
     assert U.shape == (0, m.N)
 
 
-@pytest.mark.parametrize("name,method", [("c1", 0), ("small6_240_1", 1)])
-def test_projection_period_matches_every_step(name, method):
-    """Projecting the Lanczos vectors every m-th step (H commutes with Q) gives the same chi0 G as
-    projecting every step, to the Sternheimer tolerance times the condition number."""
-    m = model(name)
-    G, _ = m.perturbations()
-    om = W.srft_sketch(G.shape[1], 4, 0)
-    kw = dict(method=method, sketch=om, id_tol=1e-9, n_cheb=16, stern_tol=1e-13)
-    U1, _ = context(name, project_every=1, **kw).apply_chi0(to_gpu(G))
-    Ua, _ = context(name, **kw).apply_chi0(to_gpu(G))
-    U8, _ = context(name, project_every=8, **kw).apply_chi0(to_gpu(G))
-    assert rel(to_np(Ua), to_np(U1)) < 1e-10
-    assert rel(to_np(U8), to_np(U1)) < 1e-10
-
-
 def test_multishift_storage_variants_agree():
     """The stored-basis multi-shift solver and the per-shift-vector solver give the same chi0~ G."""
     name = "small6_240_1"
