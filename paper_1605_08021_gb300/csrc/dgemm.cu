@@ -10,11 +10,20 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
 
+// Split over K (gridDim.z > 1): slice z takes k in [z kchunk, (z+1) kchunk) and writes its own
+// C block at C + z cz (the partial sums are added up by slice_sum_kernel).
 template <bool TA, bool TB, bool HAD>
 __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha, const double* __restrict__ A,
                                                     int lda, const double* __restrict__ B, int ldb, double beta,
                                                     double* __restrict__ C, int ldc, const double* __restrict__ Hz,
-                                                    int ldh) {
+                                                    int ldh, int kchunk, size_t cz) {
+  if (gridDim.z > 1) {
+    const int kz0 = blockIdx.z * kchunk;
+    K = min(K - kz0, kchunk);
+    A += TA ? (size_t)kz0 : (size_t)kz0 * lda;
+    B += TB ? (size_t)kz0 * ldb : (size_t)kz0;
+    C += blockIdx.z * cz;
+  }
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x;
@@ -82,11 +91,23 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
 
 template <bool TA, bool TB>
 void launch(dim3 g, cudaStream_t s, int m, int n, int k, double alpha, const double* A, int lda, const double* B,
-            int ldb, double beta, double* C, int ldc, const double* hz, int ldh) {
+            int ldb, double beta, double* C, int ldc, const double* hz, int ldh, int kchunk = 0, size_t cz = 0) {
   if (hz)
-    dgemm_kernel<TA, TB, true><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, hz, ldh);
+    dgemm_kernel<TA, TB, true><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, hz, ldh, kchunk, cz);
   else
-    dgemm_kernel<TA, TB, false><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, hz, ldh);
+    dgemm_kernel<TA, TB, false><<<g, 256, 0, s>>>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, hz, ldh, kchunk, cz);
+}
+
+// C = alpha * sum_z P[z] (+ beta C), column-major m x n with leading dimension ldc; P slices m x n.
+__global__ void slice_sum_kernel(int m, int n, int slices, const double* __restrict__ P, double alpha, double beta,
+                                 double* __restrict__ C, int ldc) {
+  const size_t total = (size_t)m * n, mn = (size_t)m * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < slices; ++z) acc += P[z * mn + e];
+    double* c = &C[(e % m) + (e / m) * (size_t)ldc];
+    *c = alpha * acc + (beta == 0.0 ? 0.0 : beta * *c);
+  }
 }
 
 }  // namespace
@@ -114,6 +135,37 @@ acp_status dgemm(acp_ctx* ctx, bool ta, bool tb, int m, int n, int k, double alp
     launch<false, false>(g, ctx->stream, m, n, 0, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, 0);
     ACP_LAUNCH(ctx);
     return ACP_OK;
+  }
+  // Few output tiles and a long K (the projector's h Psi^T X): split K over gridDim.z so that
+  // the launch fills the GPU, then add the slices up.
+  const long long tiles = (long long)g.x * g.y;
+  if (!hz && tiles < 152 && k >= 1024) {
+    int slices = (int)((304 + tiles - 1) / tiles);
+    if (slices > k / 256) slices = k / 256;
+    if (slices > 64) slices = 64;
+    if (slices >= 2) {
+      const int kchunk = ((k + slices - 1) / slices + BK - 1) / BK * BK;
+      slices = (k + kchunk - 1) / kchunk;
+      double* part = nullptr;
+      const size_t mn = (size_t)m * n;
+      ACP_TRY(ws(ctx, "dgemm_slices", mn * slices, &part));
+      ::acp::note_launch(ctx);
+      cudaEvent_t ev0 = prof_begin(ctx);
+      const dim3 gz(g.x, g.y, slices);
+      if (ta && !tb) launch<true, false>(gz, ctx->stream, m, n, k, 1.0, A, lda, B, ldb, 0.0, part, m, nullptr, 0, kchunk, mn);
+      else if (!ta && !tb) launch<false, false>(gz, ctx->stream, m, n, k, 1.0, A, lda, B, ldb, 0.0, part, m, nullptr, 0, kchunk, mn);
+      else if (!ta && tb) launch<false, true>(gz, ctx->stream, m, n, k, 1.0, A, lda, B, ldb, 0.0, part, m, nullptr, 0, kchunk, mn);
+      else launch<true, true>(gz, ctx->stream, m, n, k, 1.0, A, lda, B, ldb, 0.0, part, m, nullptr, 0, kchunk, mn);
+      ACP_LAUNCH(ctx);
+      size_t blocks = (mn + 255) / 256;
+      if (blocks > 4096) blocks = 4096;
+      ::acp::note_launch(ctx);
+      slice_sum_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(m, n, slices, part, alpha, beta, C, ldc);
+      ACP_LAUNCH(ctx);
+      prof_end(ctx, "dgemm", ev0, 2.0 * m * n * k,
+               8.0 * ((double)m * k + (double)k * n + (double)m * n * (beta != 0.0 ? 2 : 1)));
+      return ACP_OK;
+    }
   }
   ::acp::note_launch(ctx);
   const double e_flops = 2.0 * m * n * k;
