@@ -199,6 +199,30 @@ acp_status acp_compress(acp_ctx* ctx, const double* G_d, int ncol, int cap, int*
    device workspace: v_eff_d, psi_d device (N and N x n_orb), eps_h host (n_orb, ascending). */
 acp_status acp_update(acp_ctx* ctx, const double* v_eff_d, const double* psi_d, const double* eps_h, int n_orb);
 
+/* ---- projector without device allocation (no counterpart in the paper) ------------------ */
+
+/* Y = Q X = X - Psi (h Psi^T X), the projector of acp_project, for callers that must not
+   allocate device memory: code on a latency-critical stream, where cudaMalloc and cudaFree can
+   synchronise the whole device and stall other work, and host applications whose own memory
+   pool already holds the device memory, so that a further cudaMalloc fails.  It takes no
+   context and calls no cudaMalloc, cudaFree or allocating library routine.
+   psi_d: n_grid x n_orb orbitals (device, column-major, leading dimension n_grid, normalised with
+   weight h); X_d, Y_d: n_grid x ncol (device, column-major, leading dimension n_grid); Y_d may
+   equal X_d; stream: cudaStream_t (NULL = legacy default stream).  The work is enqueued on the
+   stream and the call returns without waiting for it.
+   The intermediate h Psi^T X is kept in one fixed device array of 1,048,576 doubles (8 MiB) that
+   every GPU which loads the library holds until the process exits, so n_orb * ncol may not exceed
+   1,048,576.  All calls share that array and it keeps the last call's contents; every entry a
+   call reads is written by the same call first, so nothing needs clearing, but calls that
+   overlap on the GPU (on different streams, or from different threads) race on it.  The first
+   call on each device looks up the array's device address (cudaGetSymbolAddress); make that
+   first call before any stream capture.
+   Errors: ACP_E_ARG (null pointer, n_grid, n_orb or h not positive, ncol negative, or
+   n_orb * ncol above the maximum; nothing is enqueued), ACP_E_CUDA (the address lookup or a
+   launch failed). */
+acp_status acp_project_noalloc(const double* psi_d, int n_grid, int n_orb, double h, const double* X_d, int ncol,
+                               double* Y_d, void* stream);
+
 /* ---- instrumentation (no counterpart in the paper) -------------------------------------- */
 
 /* Switch per-kernel timing on or off and clear the totals.  While on, the library records CUDA

@@ -95,6 +95,7 @@ def load():
         "acp_hamiltonian_apply": (I, [P, P, I, D, P]),
         "acp_project": (I, [P, P, I, P]),
         "acp_project_mixed": (I, [P, P, I, P]),
+        "acp_project_noalloc": (I, [P, I, I, c_double, P, I, P, P]),
         "acp_kernel_apply": (I, [P, P, I, I, P]),
         "acp_sternheimer_solve": (I, [P, P, I, D, P, POINTER(Stats)]),
         "acp_compress": (I, [P, P, I, I, POINTER(c_int), POINTER(c_int), P, D]),

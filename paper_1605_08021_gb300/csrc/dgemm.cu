@@ -2,6 +2,8 @@
 // the products W G(r_mu, :) (Eq. chi0gcompress2) and W X (Eq. dyson4), and the dynamical matrix
 // term G^T U (Eq. SecDeriv).  tcgen05 has no FP64 kind, so this path is a register-blocked DFMA
 // kernel: 64 x 64 output tiles, 16-deep shared-memory k-slices, 4 x 4 outputs per thread.
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace acp {
@@ -197,3 +199,65 @@ acp_status project(acp_ctx* ctx, const double* X, int ldx, int ncol, double* Y, 
 }
 
 }  // namespace acp
+
+// ---- projector for callers that cannot allocate device memory ----------------------------------
+// The intermediate C = h Psi^T X lives in a fixed array of device memory that the library owns
+// for the lifetime of the process (on every GPU that loads it), so this entry point needs no
+// context and no cudaMalloc.  Host code may not use the array's name as a device address: the
+// address is looked up once per device with cudaGetSymbolAddress.
+namespace acp {
+namespace {
+
+constexpr size_t kNoAllocElems = size_t(1) << 20;  // 8 MiB of FP64: n_orb * ncol <= 1,048,576
+__device__ __align__(256) double g_noalloc_c[kNoAllocElems];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[64] = {};  // per device ordinal, filled on the first call on that device
+
+}  // namespace
+
+}  // namespace acp
+
+extern "C" acp_status acp_project_noalloc(const double* psi_d, int n_grid, int n_orb, double h, const double* X_d,
+                                          int ncol, double* Y_d, void* stream) {
+  using namespace acp;
+  if (!psi_d || !X_d || !Y_d || n_grid < 1 || n_orb < 1 || ncol < 0 || !(h > 0.0)) return ACP_E_ARG;
+  if (ncol == 0) return ACP_OK;
+  if ((size_t)n_orb * (size_t)ncol > kNoAllocElems) return ACP_E_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return ACP_E_CUDA;
+  }
+  if (dev < 0 || dev >= 64) return ACP_E_ARG;
+  double* C = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_c);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return ACP_E_CUDA;
+      }
+      g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    C = g_noalloc_addr[dev];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // C = h Psi^T X: beta = 0, so every entry is written and nothing needs clearing beforehand
+  launch<true, false>(dim3((n_orb + BM - 1) / BM, (ncol + BN - 1) / BN), s, n_orb, ncol, n_grid, h, psi_d, n_grid,
+                      X_d, n_grid, 0.0, C, n_orb, nullptr, 0);
+  if (Y_d != X_d) {
+    if (cudaMemcpyAsync(Y_d, X_d, sizeof(double) * (size_t)n_grid * ncol, cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return ACP_E_CUDA;
+    }
+  }
+  // Y -= Psi C
+  launch<false, false>(dim3((n_grid + BM - 1) / BM, (ncol + BN - 1) / BN), s, n_grid, ncol, n_orb, -1.0, psi_d,
+                       n_grid, C, n_orb, 1.0, Y_d, n_grid, nullptr, 0);
+  if (cudaGetLastError() != cudaSuccess) return ACP_E_CUDA;
+  return ACP_OK;
+}
