@@ -285,6 +285,8 @@ def run_gpu(args):
                    "method": "ACP (Alg. 2 Remark + Alg. 3 + Alg. 4), " + ("FP64" if PRECISION == 0 else
                              "mixed: FP32 MINRES + 3xTF32 tcgen05 projector + FP64 refinement")},
         "rhs_pairs_per_step": pairs / args.steps, "n_mu": st["n_mu"], "alg4_iters": st["outer_iters"],
+        "lanczos_steps_per_step": sum(x["lanczos_steps"] for x in stats) / len(stats),
+        "accuracy": accuracy(D, w),
         "solve_ms_per_step": round(sum(x["ms_solve"] for x in stats) / len(stats), 2),
         "compress_ms_per_step": round(sum(x["ms_compress"] for x in stats) / len(stats), 2),
         "e2e": {"value": round(e2e_pairs_all / e2e_max, 2), "unit": UNIT,
@@ -298,6 +300,19 @@ def run_gpu(args):
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
     return line
+
+
+def accuracy(D, w):
+    """Errors against the exact dynamical matrix of the 128-atom chain written by the oracle
+    (tests/golden/c2_exact_dmat.npz): relative Frobenius error of D and max |omega - omega_ref| /
+    max |omega_ref|.  None for other workloads."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", "c2_exact_dmat.npz")
+    if WORKLOAD != "c2" or not os.path.exists(path):
+        return None
+    ref = np.load(path)
+    return {"D_rel_fro": float(np.linalg.norm(D - ref["D"]) / np.linalg.norm(ref["D"])),
+            "omega_rel": float(np.abs(w - ref["omega"]).max() / np.abs(ref["omega"]).max())}
 
 
 # ---- the oracle (CPU baseline and the reference arm) -----------------------------------------
