@@ -134,6 +134,41 @@ def config(index: int) -> System:
     raise ValueError(f"configuration {index} is not available")
 
 
+def smooth_5(n: int) -> int:
+    """Smallest integer >= n whose only prime factors are 2, 3 and 5."""
+    m = max(int(n), 1)
+    while True:
+        r = m
+        for p in (2, 3, 5):
+            while r % p == 0:
+                r //= p
+        if r == 1:
+            return m
+        m += 1
+
+
+def batch_config(index: int = 4, n_sys: int = 64, min_atoms: int = 16, max_atoms: int = 256) -> list:
+    """Configuration 4: independent 1D chains of uneven size for the batched form.
+
+    System k draws N_A uniform in [min_atoms, max_atoms], atoms every 10 bohr with uniform
+    +-0.5 displacements, Z uniform in {1, 2}, sigma 1, kappa 0.01, kernel strength s uniform in
+    [0.3, 1.0] (the depth scaling that spreads the gaps), occupation 1, and the grid N = smallest
+    2-3-5-smooth integer >= 40 N_A (h close to 0.25).  Smaller n_sys / max_atoms give the same
+    recipe at test sizes."""
+    out = []
+    for k in range(n_sys):
+        rng = _rng(index, k)
+        n_atoms = int(rng.integers(min_atoms, max_atoms + 1))
+        scale = float(rng.uniform(0.3, 1.0))
+        disp = rng.uniform(-0.5, 0.5, n_atoms)
+        Z = rng.integers(1, 3, n_atoms).astype(np.float64)
+        R = ((np.arange(n_atoms) + 0.5) * 10.0 + disp).reshape(n_atoms, 1)
+        n_grid = smooth_5(40 * n_atoms)
+        out.append(System(name=f"batch{index}_{k}_na{n_atoms}", dim=1, n=(n_grid,), L=(10.0 * n_atoms,), R=R, Z=Z,
+                          sigma=np.ones(n_atoms), mass=np.ones(n_atoms), kappa=0.01, scale=scale, occ=1))
+    return out
+
+
 def mixed_chain(n_atoms: int, n_grid: int, seed: int = 0, scale: float = 0.5) -> System:
     """Config-2 recipe at another size: atoms every 10 bohr with uniform +-0.5 displacements,
     Z uniform in {1, 2}, sigma 1, kappa 0.01, occupation 1 (for mid-size profiling runs)."""

@@ -11,6 +11,9 @@ all ranks; ``ms_per_step`` is the dynamical-matrix wall time.  The inputs (groun
 are resident in device memory before the timed region; the ``e2e`` leg copies them from pinned
 host memory every step and returns D and omega to the host.
 
+The timed form is ACP with mixed-precision solves (--precision fp64 for the FP64 form); the
+line's ``comparison`` gives the other ACP arithmetic and plain FP64 DFPT (column sample).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {acp,reference}]
 For N > 1 launch with torch.distributed.run; every rank runs an independent replica.
 """
@@ -35,11 +38,12 @@ ACP_PARAMS = dict(id_tol=1e-8, n_cheb=16, sketch_r=8, dyson_tol=1e-6, dyson_maxi
 
 
 def workload_name():
+    form = "ACP FP64" if PRECISION == 0 else "ACP mixed precision"
     if WORKLOAD == "chain64":
         return ("1D periodic rHF chain, 64 atoms (config-2 recipe at half size, N=2560) for profiler captures; "
-                f"ACP FP64 (N_c={ACP_PARAMS['n_cheb']}, id_tol={ACP_PARAMS['id_tol']:g})")
+                f"{form} (N_c={ACP_PARAMS['n_cheb']}, id_tol={ACP_PARAMS['id_tol']:g})")
     return ("1D periodic rHF chain, 128 atoms spaced 10 bohr with +-0.5 displacements, Z in {1,2}, sigma 1, "
-            "kappa 0.01, kernel scale 0.5, N=5120, 192 occupied orbitals, 128 perturbations; ACP FP64 "
+            f"kappa 0.01, kernel scale 0.5, N=5120, 192 occupied orbitals, 128 perturbations; {form} "
             f"(N_c={ACP_PARAMS['n_cheb']}, id_tol={ACP_PARAMS['id_tol']:g}, SRFT r={ACP_PARAMS['sketch_r']}, "
             f"Alg. 4 delta={ACP_PARAMS['dyson_tol']:g})")
 
@@ -241,6 +245,10 @@ def run_gpu(args):
     e2e_s = time.perf_counter() - t0
     barrier(dist)
 
+    comparison = None
+    if not args.no_compare and WORKLOAD == "c2" and rank == 0:
+        comparison = compare_forms(P, s, gs, om, V, psi, rho, R, Z, sig)
+
     ms_max = max_over_ranks(dist, ms)
     e2e_max = max_over_ranks(dist, e2e_s)
     pairs_all = sum_over_ranks(dist, pairs)
@@ -293,6 +301,7 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(V_h.numel() * 8 + psi_h.numel() * 8 + rho_h.numel() * 8 + gs.n_orb * 8),
                 "d2h_bytes_per_step": int(D2.size * 8 + w2.size * 8)},
         "gpu_launches": int(launches),
+        "comparison": comparison,
         "roofline": roof,
         "clocks": clk,
     }
@@ -300,6 +309,53 @@ def run_gpu(args):
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)
     return line
+
+
+def compare_forms(P, s, gs, om, V, psi, rho, R, Z, sig):
+    """Dynamical-matrix time of the other ACP arithmetic (FP64 when the timed form is mixed, and
+    vice versa), one warm run each, and of plain FP64 DFPT (Alg. 1 + GMRES on the Dyson equation)
+    on a sample of 4 of the 128 perturbation columns, extrapolated linearly to all columns (every
+    column's Dyson solve is independent; the sample batches fewer right-hand sides, so the
+    extrapolation does not flatter ACP)."""
+    import numpy as np
+    import torch
+    global PRECISION
+    out = {}
+    other = 1 - PRECISION
+    saved = PRECISION
+    PRECISION = other
+    try:
+        ctx = make_context(P, s, gs, om, V, psi)
+        ctx.dynamical_matrix(R, Z, sig, rho, allow_noconv=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        D, st = ctx.dynamical_matrix(R, Z, sig, rho, allow_noconv=True)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        w = ctx.phonons(D)
+        key = "acp_fp64" if other == 0 else "acp_mixed"
+        out[key] = {"D_ms": round(e0.elapsed_time(e1), 1), "rhs_solved": st["rhs_solved"],
+                    "rhs_per_s": round(st["rhs_solved"] / (e0.elapsed_time(e1) * 1e-3), 1),
+                    "accuracy": accuracy(D, w)}
+        ctx.close()
+    finally:
+        PRECISION = saved
+    o = P.options(method=P.ACP_METHOD_PLAIN, occ=float(s.occ), stern_tol=ACP_PARAMS["stern_tol"],
+                  dyson_tol=1e-10, dyson_maxit=80, precision=0)
+    ctxp = P.Context(s.n[0], s.L[0], s.kappa, s.scale, V, psi, gs.eps[: gs.n_orb], o)
+    G, _, _ = ctxp.perturbations(R, Z, sig)
+    Gs = G[:4].contiguous()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    U, st = ctxp.dyson_solve(Gs, allow_noconv=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out["plain_fp64"] = {"sample_columns": 4, "sample_ms": round(dt * 1e3, 1),
+                         "D_ms_extrapolated": round(dt * 1e3 * s.n_pert / 4, 1),
+                         "rhs_solved_sample": st["rhs_solved"], "gmres_iters": st["outer_iters"]}
+    ctxp.close()
+    return out
 
 
 def accuracy(D, w):
@@ -392,9 +448,11 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["acp", "reference"], default="acp")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the comparison with the other ACP arithmetic and with plain FP64 DFPT")
     ap.add_argument("--workload", choices=["c2", "chain64"], default="c2",
                     help="c2: the benchmark configuration; chain64: half-size chain for profiler captures")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed",
                     help="arithmetic of the Sternheimer solves")
     args = ap.parse_args(argv)
     global WORKLOAD, PRECISION

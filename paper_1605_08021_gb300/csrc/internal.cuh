@@ -79,6 +79,8 @@ struct acp_ctx {
   float* d_psiT_lo = nullptr;
   bool psi32_stale = true;
   bool tables32_stale = true;     // FP32 copies of the kinetic symbol, V_eff and twiddles
+  std::map<long long, std::pair<int, int>> tc_tune;  // projector tile choice per shape
+  bool mixed_refine = true;       // mixed precision: refine the multi-shift solves to stern_tol
   acp::FftPlan plan;
   acp::Workspace ws;
   acp::Profiler prof;

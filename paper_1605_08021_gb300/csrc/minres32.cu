@@ -54,6 +54,7 @@ struct M32 {
   float *V, *Vp, *P, *W1, *W2;         // ld x ncol
   float *alpha, *beta;                 // ncol (Lanczos coefficients, read by the spectral kernel)
   double *beta1, *cs, *sn, *dbar, *epsln, *phibar;
+  const double* tolc;                  // per-column relative tolerance (nullable: the scalar one)
   int *active, *iters;
   int ld;
 };
@@ -119,7 +120,8 @@ __global__ void __launch_bounds__(kThreads) m32_step_kernel(int N, M32 s, float*
     const int it = s.iters[j] + 1;
     s.iters[j] = it;
     const bool bad = !isfinite(bn) || !isfinite(pbn);
-    if (bad || fabs(pbn) <= tol * s.beta1[j] || bn == 0.0 || it >= maxit) s.active[j] = 0;
+    const double tj = s.tolc ? s.tolc[j] : tol;
+    if (bad || fabs(pbn) <= tj * s.beta1[j] || bn == 0.0 || it >= maxit) s.active[j] = 0;
   }
   __syncthreads();
   const float oe = coef[0], de = coef[1], ig = coef[2], ph = coef[3];
@@ -178,10 +180,13 @@ __global__ void __launch_bounds__(kThreads) scale_to_f32_kernel(int N, int ld32,
 
 // After the FP32 projection of R32: the projected residual norm is ||R32_j|| * scale_j.  Columns at
 // or below tol (relative to ||B_j||) are converged: masked, and their R32 zeroed.
+// The inner solve of column j only has to reduce its residual by the factor tol / rel_j that is
+// still missing (with a margin of 4, never below the FP32 floor kInnerTol, never above 1e-2).
 __global__ void __launch_bounds__(kThreads) refine_check_kernel(int N, int ld32, float* __restrict__ R32,
                                                                 const double* __restrict__ scale,
                                                                 const double* __restrict__ bnorm, double tol,
-                                                                double* __restrict__ rel, int* __restrict__ act) {
+                                                                double* __restrict__ rel, int* __restrict__ act,
+                                                                double* __restrict__ tol_in, double floor_tol) {
   __shared__ float red[32];
   const int j = blockIdx.x;
   float* o = R32 + (size_t)j * ld32;
@@ -196,6 +201,8 @@ __global__ void __launch_bounds__(kThreads) refine_check_kernel(int N, int ld32,
   if (threadIdx.x == 0) {
     rel[j] = rl;
     act[j] = go ? 1 : 0;
+    const double want = (rl > 0.0) ? 0.25 * tol / rl : 1e-2;
+    tol_in[j] = fmin(1e-2, fmax(floor_tol, want));
   }
 }
 
@@ -449,7 +456,7 @@ acp_status sum_iters(acp_ctx* ctx, const int* iters, int n, long long* steps, lo
 
 // FP32 inner solve of Q(H - s_j)Q D_j = R32_j (R32 projected, unit or zero columns).
 acp_status minres32(acp_ctx* ctx, const float* R32, int ncol, const float* shift32, float* D32, double tol,
-                    long long* steps, long long* max_it, double t0_ms) {
+                    const double* tolc, long long* steps, long long* max_it, double t0_ms) {
   const int N = ctx->N, ld = ctx->ld32;
   const size_t nv = (size_t)ld * ncol;
   M32 s{};
@@ -467,6 +474,7 @@ acp_status minres32(acp_ctx* ctx, const float* R32, int ncol, const float* shift
   s.beta1 = dsc; s.cs = dsc + ncol; s.sn = dsc + 2 * ncol; s.dbar = dsc + 3 * ncol; s.epsln = dsc + 4 * ncol;
   s.phibar = dsc + 5 * ncol;
   s.active = iv; s.iters = iv + ncol;
+  s.tolc = tolc;
   ::acp::note_launch(ctx);
   m32_init_kernel<<<ncol, kThreads, 0, ctx->stream>>>(N, R32, s, D32);
   ACP_LAUNCH(ctx);
@@ -500,7 +508,7 @@ acp_status refine(acp_ctx* ctx, const double* B, int ncol, const double* shift_d
   int* act = nullptr;
   ACP_TRY(ws(ctx, "rf_r", nv, &R));
   ACP_TRY(ws(ctx, "rf_y", nv, &Y));
-  ACP_TRY(ws(ctx, "rf_dsc", 3 * (size_t)ncol, &dsc));
+  ACP_TRY(ws(ctx, "rf_dsc", 4 * (size_t)ncol, &dsc));
   ACP_TRY(ws(ctx, "rf_r32", (size_t)ld * ncol, &R32));
   ACP_TRY(ws(ctx, "rf_d32", (size_t)ld * ncol, &D32));
   ACP_TRY(ws(ctx, "rf_sh32", (size_t)ncol, &sh32));
@@ -508,6 +516,7 @@ acp_status refine(acp_ctx* ctx, const double* B, int ncol, const double* shift_d
   double* bnorm = dsc;
   double* scale = dsc + ncol;
   double* rel = dsc + 2 * ncol;
+  double* tol_in = dsc + 3 * ncol;
   ACP_CUDA(ctx, cudaMemsetAsync(R32, 0, sizeof(float) * ld * ncol, ctx->stream));
   ::acp::note_launch(ctx);
   col_norms64<<<(ncol * 32 + 255) / 256, 256, 0, ctx->stream>>>(N, ncol, B, bnorm);
@@ -527,20 +536,20 @@ acp_status refine(acp_ctx* ctx, const double* B, int ncol, const double* shift_d
   }
   ACP_CUDA(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
   const double tol = ctx->opt.stern_tol;
-  const double tol_in = tol > kInnerTol ? tol : kInnerTol;
   for (int round = 0;; ++round) {
     ::acp::note_launch(ctx);
     scale_to_f32_kernel<<<ncol, kThreads, 0, ctx->stream>>>(N, ld, R, R32, scale, ctx->d_flag);
     ACP_LAUNCH(ctx);
     ACP_TRY(project32(ctx, R32, ld, ncol, R32, ld));
     ::acp::note_launch(ctx);
-    refine_check_kernel<<<ncol, kThreads, 0, ctx->stream>>>(N, ld, R32, scale, bnorm, tol, rel, act);
+    refine_check_kernel<<<ncol, kThreads, 0, ctx->stream>>>(N, ld, R32, scale, bnorm, tol, rel, act, tol_in,
+                                                            kInnerTol);
     ACP_LAUNCH(ctx);
     int n_act = 0;
     ACP_TRY(count32(ctx, act, ncol, &n_act));
     if (n_act == 0 || round == kMaxRounds) break;
     if (deadline_passed(ctx, t0_ms)) return set_error(ctx, ACP_E_TIMEOUT, "deadline passed in refinement");
-    ACP_TRY(minres32(ctx, R32, ncol, sh32, D32, tol_in, &rep->steps, &rep->max_iters, t0_ms));
+    ACP_TRY(minres32(ctx, R32, ncol, sh32, D32, kInnerTol, tol_in, &rep->steps, &rep->max_iters, t0_ms));
     ::acp::note_launch(ctx);
     refine_update_kernel<<<grid_for(nv), 256, 0, ctx->stream>>>(N, ncol, ld, D32, scale, act, X);
     ACP_LAUNCH(ctx);
@@ -658,6 +667,7 @@ acp_status minres_multishift_mixed(acp_ctx* ctx, const double* B, int nmu, const
   msb32_assemble_kernel<<<dim3((N + 255) / 256, nmu), 256, 0, ctx->stream>>>(N, nmu, nc, s, bsc, X);
   ACP_LAUNCH(ctx);
   ACP_TRY(sum_iters(ctx, s.iters, nmu, &rep->steps, &rep->max_iters));
+  if (!ctx->mixed_refine) return ACP_OK;  // inexact outer iteration: the FP32 pass is the answer
   // ---- refinement of every (shift, point) pair ----------------------------------------------
   double *Brep = nullptr, *shifts = nullptr;
   const size_t ncol = nq;

@@ -385,7 +385,18 @@ acp_status dyson_acp(acp_ctx* ctx, const double* G, int ncol, double* U, acp_sta
   int it = 0;
   double change = 1e300;
   const int maxit = ctx->opt.dyson_maxit > 0 ? ctx->opt.dyson_maxit : 8;
+  // Mixed precision: while the iterates still change by more than kRefineSwitch, the compressed
+  // equations are solved by the FP32 pass alone (an inexact outer iteration, whose error ~1e-6
+  // is below the change); from then on every solve is refined to stern_tol, and Alg. 4 may only
+  // stop after a refined iteration.
+  constexpr double kRefineSwitch = 1e-4;
+  const bool mixed = ctx->opt.precision == ACP_PREC_MIXED;
+  struct RefineReset {
+    acp_ctx* c;
+    ~RefineReset() { c->mixed_refine = true; }
+  } reset{ctx};
   for (it = 0; it < maxit; ++it) {
+    ctx->mixed_refine = !mixed || change <= kRefineSwitch || it == maxit - 1;
     ACP_TRY(spectral_apply(ctx, Ut, N, ncol, MULT_KHAT, false, nullptr, Gk, N, nullptr, nullptr));
     Compression comp;
     double* W = nullptr;
@@ -412,7 +423,7 @@ acp_status dyson_acp(acp_ctx* ctx, const double* G, int ncol, double* U, acp_sta
     double* t = Ut; Ut = Un; Un = t;
     if (st) st->n_mu = k;
     if (!std::isfinite(change)) return set_error(ctx, ACP_E_NUMERIC, "NaN in the adaptive Dyson iteration");
-    if (change < ctx->opt.dyson_tol) { ++it; break; }
+    if (change < ctx->opt.dyson_tol && ctx->mixed_refine) { ++it; break; }
     if (deadline_passed(ctx, t0)) return set_error(ctx, ACP_E_TIMEOUT, "deadline passed in Alg. 4");
   }
   // U = U~ - B

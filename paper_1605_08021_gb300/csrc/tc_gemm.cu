@@ -171,11 +171,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int row = m0 + q * 32 + lane;
       const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
       for (int c0 = 0; c0 < p.BN; c0 += 32) {
+        const int col0 = n0 + c0;
+        const int nvalid = (row < p.M) ? min(min(32, p.BN - c0), p.Nd - col0) : 0;
+        float4 xv[8];
+        if (p.mode == 1 && nvalid == 32) {
+          // issue the loads of X before waiting on the accumulator
+          const float4* x4 = reinterpret_cast<const float4*>(p.X + (size_t)row * p.ldx + col0);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) xv[j] = __ldg(x4 + j);
+        }
         float v[32];
         tc::tmem_ld_32x32(trow + (uint32_t)c0, v);
-        if (row >= p.M) continue;
-        const int col0 = n0 + c0;
-        const int nvalid = min(min(32, p.BN - c0), p.Nd - col0);
         if (nvalid <= 0) continue;
         if (p.mode == 0) {
           float* o = p.out + (size_t)blockIdx.y * p.slice_stride + (size_t)row * p.ldo + col0;
@@ -186,15 +192,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int j = 0; j < nvalid; ++j) o[j] = v[j];
           }
         } else {
-          const float* x = p.X + (size_t)row * p.ldx + col0;
           float* y = p.Y + (size_t)row * p.ldy + col0;
           if (nvalid == 32) {
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              const float4 xv = *reinterpret_cast<const float4*>(x + j);
-              *reinterpret_cast<float4*>(y + j) = make_float4(xv.x - v[j], xv.y - v[j + 1], xv.z - v[j + 2], xv.w - v[j + 3]);
-            }
+            for (int j = 0; j < 8; ++j)
+              *reinterpret_cast<float4*>(y + 4 * j) =
+                  make_float4(xv[j].x - v[4 * j], xv[j].y - v[4 * j + 1], xv[j].z - v[4 * j + 2], xv[j].w - v[4 * j + 3]);
           } else {
+            const float* x = p.X + (size_t)row * p.ldx + col0;
             for (int j = 0; j < nvalid; ++j) y[j] = x[j] - v[j];
           }
         }
@@ -325,12 +330,13 @@ acp_status mixed_prepare(acp_ctx* ctx) {
   return ACP_OK;
 }
 
-acp_status project32(acp_ctx* ctx, const float* X, int ldx, int ncol, float* Y, int ldy) {
-  if (ncol <= 0) return ACP_OK;
-  ACP_TRY(mixed_prepare(ctx));
+namespace {
+
+// One projector application with a given tile configuration: GEMM 1 over `slices` K-slices
+// (0: automatic, about one CTA per SM), GEMM 2 with output tiles 128 x bn2.
+acp_status project32_cfg(acp_ctx* ctx, const float* X, int ldx, int ncol, float* Y, int ldy, int bn2,
+                         int slice_mul) {
   const int N = ctx->N, no = ctx->n_orb, no_pad = ctx->no_pad;
-  if ((ldx % 4) || (ldy % 4) || ldx < N || ldy < N)
-    return set_error(ctx, ACP_E_ARG, "FP32 blocks need a leading dimension >= N and a multiple of 4");
   int* status = ctx->d_flag + 8;
   const int m_tiles = (ncol + kBM - 1) / kBM;
 
@@ -339,7 +345,7 @@ acp_status project32(acp_ctx* ctx, const float* X, int ldx, int ncol, float* Y, 
   int bn1 = (no + n_tiles1 - 1) / n_tiles1;
   bn1 = (bn1 + 15) / 16 * 16;
   const int kb_total1 = (N + kBK - 1) / kBK;
-  int slices = 148 / (m_tiles * n_tiles1);
+  int slices = 148 * slice_mul / (m_tiles * n_tiles1);
   if (slices < 1) slices = 1;
   if (slices > kb_total1) slices = kb_total1;
   const int kb_per1 = (kb_total1 + slices - 1) / slices;
@@ -368,10 +374,10 @@ acp_status project32(acp_ctx* ctx, const float* X, int ldx, int ncol, float* Y, 
   a1.ldo = no_pad;
   a1.slice_stride = slice_stride;
   a1.status = status;
-  const double fl1 = 2.0 * (double)ncol * no * N;  // algorithmic (the tensor pipe runs 3 passes)
+  const double fl = 2.0 * (double)ncol * no * N;  // algorithmic (the tensor pipe runs 3 passes)
   cudaEvent_t ev = prof_begin(ctx);
   ACP_TRY(launch_tc3(ctx, dim3(m_tiles, slices, n_tiles1), mX, mX, mPh, mPl, a1));
-  prof_end(ctx, "tc_gemm", ev, fl1, 4.0 * ((double)ncol * N + 2.0 * no * N + (double)slices * ncol * no));
+  prof_end(ctx, "tc_gemm", ev, fl, 4.0 * ((double)ncol * N + 2.0 * no * N + (double)slices * ncol * no));
 
   {
     size_t blocks = ((size_t)slice_stride + 255) / 256;
@@ -383,7 +389,7 @@ acp_status project32(acp_ctx* ctx, const float* X, int ldx, int ncol, float* Y, 
   }
 
   // GEMM 2: Y^T = X^T - C^T Psi^T
-  const int bn2 = (N >= 256) ? 256 : (N + 15) / 16 * 16;
+  if (N < bn2) bn2 = (N + 15) / 16 * 16;
   ACP_TRY(make_map(ctx, &mCh, ct_hi, no_pad, ncol, no_pad, kBM));
   ACP_TRY(make_map(ctx, &mCl, ct_lo, no_pad, ncol, no_pad, kBM));
   ACP_TRY(make_map(ctx, &mTh, ctx->d_psiT_hi, no_pad, N, no_pad, bn2));
@@ -402,11 +408,60 @@ acp_status project32(acp_ctx* ctx, const float* X, int ldx, int ncol, float* Y, 
   a2.Y = Y;
   a2.ldy = ldy;
   a2.status = status;
-  const double fl2 = 2.0 * (double)ncol * no * N;
   ev = prof_begin(ctx);
   ACP_TRY(launch_tc3(ctx, dim3(m_tiles, 1, (N + bn2 - 1) / bn2), mCh, mCl, mTh, mTl, a2));
-  prof_end(ctx, "tc_gemm", ev, fl2, 4.0 * (2.0 * ncol * N + 2.0 * no * N + 2.0 * (double)ncol * no_pad));
+  prof_end(ctx, "tc_gemm", ev, fl, 4.0 * (2.0 * ncol * N + 2.0 * no * N + 2.0 * (double)ncol * no_pad));
   return ACP_OK;
+}
+
+constexpr int kTileCandidates[][2] = {{256, 1}, {128, 1}, {64, 1}, {256, 2}, {128, 2}};
+
+}  // namespace
+
+// Y = Q X.  The tile configuration (GEMM 2 tile width, GEMM 1 K-slices) is chosen per problem
+// shape by timing every candidate once on the caller's data (Q is idempotent, so the extra
+// applications leave Y = Q X unchanged up to rounding) and kept in the context.
+acp_status project32(acp_ctx* ctx, const float* X, int ldx, int ncol, float* Y, int ldy) {
+  if (ncol <= 0) return ACP_OK;
+  ACP_TRY(mixed_prepare(ctx));
+  const int N = ctx->N;
+  if ((ldx % 4) || (ldy % 4) || ldx < N || ldy < N)
+    return set_error(ctx, ACP_E_ARG, "FP32 blocks need a leading dimension >= N and a multiple of 4");
+  int lg = 0;
+  while ((1 << (lg + 1)) <= ncol) ++lg;
+  const long long key = ((long long)lg << 48) ^ ((long long)N << 20) ^ (long long)ctx->n_orb;
+  auto it = ctx->tc_tune.find(key);
+  if (it == ctx->tc_tune.end()) {
+    // first application at this shape: Y = Q X once, then time each candidate on Y in place
+    ACP_TRY(project32_cfg(ctx, X, ldx, ncol, Y, ldy, 256, 1));
+    const bool prof_on = ctx->prof.on;
+    ctx->prof.on = false;
+    cudaEvent_t e0, e1;
+    ACP_CUDA(ctx, cudaEventCreate(&e0));
+    ACP_CUDA(ctx, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_i = 0;
+    const int ncand = (int)(sizeof(kTileCandidates) / sizeof(kTileCandidates[0]));
+    for (int c = 0; c < ncand; ++c) {
+      ACP_TRY(project32_cfg(ctx, Y, ldy, ncol, Y, ldy, kTileCandidates[c][0], kTileCandidates[c][1]));  // warm
+      ACP_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+      ACP_TRY(project32_cfg(ctx, Y, ldy, ncol, Y, ldy, kTileCandidates[c][0], kTileCandidates[c][1]));
+      ACP_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+      ACP_CUDA(ctx, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      ACP_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_i = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->prof.on = prof_on;
+    ctx->tc_tune[key] = {kTileCandidates[best_i][0], kTileCandidates[best_i][1]};
+    return ACP_OK;
+  }
+  return project32_cfg(ctx, X, ldx, ncol, Y, ldy, it->second.first, it->second.second);
 }
 
 namespace {
