@@ -128,7 +128,7 @@ def scf(sysm: System, tol: float = 1e-11, maxit: int = 200, beta: float = 0.3, h
         V = np.load(cache_file)
         w, psi, rho = solve(V)
         res = np.linalg.norm(potential(rho) - V) / max(np.linalg.norm(V), 1e-300)
-        if res < 1e-7:
+        if res < max(1e-7, 100.0 * tol):
             return GroundState(V=V, psi=np.asfortranarray(psi), eps=w, rho=rho, m=m, n_orb=n_orb,
                                scf_residual=float(res), iterations=0, seconds=time.time() - t0)
         V_start = V

@@ -162,13 +162,14 @@ def build_inputs():
 
 
 PRECISION = 0
+USE_GRAPHS = 0
 
 
 def make_context(P, s, gs, om, V, psi):
     o = P.options(method=P.ACP_METHOD_ACP, occ=float(s.occ), sketch=om, id_tol=ACP_PARAMS["id_tol"],
                   n_cheb=ACP_PARAMS["n_cheb"], dyson_tol=ACP_PARAMS["dyson_tol"],
                   dyson_maxit=ACP_PARAMS["dyson_maxit"], stern_tol=ACP_PARAMS["stern_tol"],
-                  precision=PRECISION)
+                  precision=PRECISION, use_graphs=USE_GRAPHS)
     return P.Context(s.n[0], s.L[0], s.kappa, s.scale, V, psi, gs.eps[: gs.n_orb], o)
 
 
@@ -454,8 +455,12 @@ def main(argv=None):
                     help="c2: the benchmark configuration; chain64: half-size chain for profiler captures")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed",
                     help="arithmetic of the Sternheimer solves")
+    ap.add_argument("--graphs", action="store_true",
+                    help="replay the FP32 Lanczos chunks as CUDA graphs (graph-replayed kernels are not in the "
+                         "per-kernel profile)")
     args = ap.parse_args(argv)
-    global WORKLOAD, PRECISION
+    global WORKLOAD, PRECISION, USE_GRAPHS
+    USE_GRAPHS = 1 if args.graphs else 0
     WORKLOAD = args.workload
     PRECISION = 1 if args.precision == "mixed" else 0
     if args.impl == "reference":

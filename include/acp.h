@@ -104,6 +104,9 @@ typedef struct {
                           vectors), 1 stored basis, 2 per-shift vectors.  A stored-basis solve that
                           needs more steps than its basis holds returns ACP_E_NOCONV.              */
   int precision;       /* ACP_PREC_FP64 or ACP_PREC_MIXED (see above)                            */
+  int use_graphs;      /* mixed precision: capture 16-step chunks of the FP32 Lanczos loops once as
+                          CUDA graphs and replay them (1), or launch every kernel (0).  Kernels
+                          replayed from graphs are not timed by acp_profile_*.                      */
 } acp_options;
 
 typedef struct {
@@ -158,6 +161,21 @@ acp_status acp_perturbations(acp_ctx* ctx, const acp_atoms* atoms, double* G_d, 
    U_d: optional N x (dim n_atoms) output of chi G (NULL: internal). */
 acp_status acp_dynamical_matrix(acp_ctx* ctx, const acp_atoms* atoms, const double* rho_d,
                                 double* D_h, double* U_d, acp_stats* stats);
+
+/* Batched form: the dynamical matrices of n_sys independent systems of uneven size, one context
+   per system (created by the caller, each on its own CUDA stream so that the systems run
+   concurrently; contexts sharing a stream serialise).  A pool of n_workers host threads (0: one
+   per hardware thread, at most 64) takes systems from a work queue, largest grid first, and runs
+   acp_dynamical_matrix on each: the per-system phases (compression, Alg. 4 updates, D) of
+   different systems overlap on their streams, and with use_graphs set in the contexts' options
+   every 16-step chunk of the FP32 Lanczos loops is one CUDA graph launch.  atoms[i], rho_d[i],
+   D_h[i] and stats[i] (nullable) are system i's arguments of acp_dynamical_matrix;
+   status_out (nullable, n_sys entries) receives each system's status.  Returns ACP_OK, or the
+   first failing system's status (the others still run).  No counterpart in the paper, which
+   treats one system at a time. */
+acp_status acp_batch_dynamical_matrix(acp_ctx* const* ctxs, int n_sys, const acp_atoms* atoms,
+                                      const double* const* rho_d, double* const* D_h, acp_stats* stats,
+                                      acp_status* status_out, int n_workers);
 
 /* Phonon frequencies of a symmetric n x n host matrix D (Sec. 2.2, D u = omega^2 u) by a
    cyclic Jacobi eigensolver on the device: omega_h[k] = sign(lambda_k) sqrt(|lambda_k|),

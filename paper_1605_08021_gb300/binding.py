@@ -52,7 +52,8 @@ class Options(ctypes.Structure):
                 ("sketch_cols", c_int), ("sketch", POINTER(c_double)), ("max_rank", c_int),
                 ("stern_tol", c_double), ("stern_maxit", c_int), ("dyson_tol", c_double),
                 ("dyson_maxit", c_int), ("rhs_batch", c_int), ("deadline_s", c_double),
-                ("project_every", c_int), ("ms_variant", c_int), ("precision", c_int)]
+                ("project_every", c_int), ("ms_variant", c_int), ("precision", c_int),
+                ("use_graphs", c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -92,6 +93,8 @@ def load():
         "acp_perturbations": (I, [P, POINTER(Atoms), P, P, P]),
         "acp_dynamical_matrix": (I, [P, POINTER(Atoms), P, D, P, POINTER(Stats)]),
         "acp_phonons": (I, [P, D, I, D, D]),
+        "acp_batch_dynamical_matrix": (I, [POINTER(P), I, POINTER(Atoms), POINTER(P), POINTER(D), POINTER(Stats),
+                                           POINTER(c_int), I]),
         "acp_hamiltonian_apply": (I, [P, P, I, D, P]),
         "acp_project": (I, [P, P, I, P]),
         "acp_project_mixed": (I, [P, P, I, P]),
@@ -133,12 +136,12 @@ def _check_block(t, N, name):
 
 def options(method=ACP_METHOD_ACP, occ=1.0, n_cheb=16, id_tol=1e-5, sketch=None, max_rank=0,
             stern_tol=1e-11, stern_maxit=5000, dyson_tol=1e-10, dyson_maxit=30, rhs_batch=0,
-            deadline_s=0.0, project_every=0, ms_variant=0, precision=0):
+            deadline_s=0.0, project_every=0, ms_variant=0, precision=0, use_graphs=0):
     """Options as a dict (the sketch Omega, if given, is an (n_cols, r) float64 array)."""
     return dict(method=method, occ=occ, n_cheb=n_cheb, id_tol=id_tol, sketch=sketch, max_rank=max_rank,
                 stern_tol=stern_tol, stern_maxit=stern_maxit, dyson_tol=dyson_tol, dyson_maxit=dyson_maxit,
                 rhs_batch=rhs_batch, deadline_s=deadline_s, project_every=project_every,
-                ms_variant=ms_variant, precision=precision)
+                ms_variant=ms_variant, precision=precision, use_graphs=use_graphs)
 
 
 class Context:
@@ -197,6 +200,7 @@ class Context:
         o.project_every = int(d.get("project_every", 0))
         o.ms_variant = int(d.get("ms_variant", 0))
         o.precision = int(d.get("precision", 0))
+        o.use_graphs = int(d.get("use_graphs", 0))
         self._opts = o
         return o
 
@@ -342,3 +346,34 @@ class Context:
                                          _tptr(Xi), _dptr(rd)))
         k = n_mu.value
         return k, np.array(piv[:k], dtype=np.int64), Xi[:k], rd[:k]
+
+
+def batch_dynamical_matrix(contexts, atoms, rhos, n_workers=0):
+    """acp_batch_dynamical_matrix over several contexts (one per system, each on its own stream).
+
+    atoms: one (R, Z, sigma) per system (host arrays); rhos: one float64 CUDA density per system.
+    Returns (list of D, list of stats dicts, list of status names).  Raises AcpError only for an
+    invalid call; per-system failures are reported in the status list.
+    """
+    lib = load()
+    n = len(contexts)
+    keep = []
+    ctx_arr = (c_void_p * n)(*[c.ptr.value for c in contexts])
+    at = (Atoms * n)()
+    Ds = []
+    for i, (R, Z, sig) in enumerate(atoms):
+        arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).ravel()) for a in (R, Z, sig)]
+        keep.append(arrs)
+        at[i].n_atoms = int(arrs[1].size)
+        at[i].R, at[i].Z, at[i].sigma = (_dptr(x) for x in arrs)
+        at[i].mass = None
+        Ds.append(np.zeros((arrs[1].size, arrs[1].size)))
+    rho_arr = (c_void_p * n)(*[r.data_ptr() for r in rhos])
+    D_arr = (POINTER(c_double) * n)(*[_dptr(D) for D in Ds])
+    st = (Stats * n)()
+    status = (c_int * n)()
+    rc = lib.acp_batch_dynamical_matrix(ctx_arr, n, at, rho_arr, D_arr, st, status, int(n_workers))
+    if rc == 1 and all(x == 0 for x in status):
+        raise AcpError(rc, "invalid batch arguments")
+    return Ds, [x.as_dict() for x in st], [STATUS.get(x, str(x)) for x in status]
+

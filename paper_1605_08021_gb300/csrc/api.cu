@@ -1,6 +1,10 @@
 // C ABI entry points (include/acp.h): context life cycle, workspace, options and dispatch.
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstring>
+#include <mutex>
+#include <thread>
 
 #include "internal.cuh"
 
@@ -29,6 +33,11 @@ acp_status set_error(acp_ctx* ctx, acp_status st, const char* fmt, ...) {
   return st;
 }
 
+std::mutex& device_mutex() {
+  static std::mutex mu;
+  return mu;
+}
+
 acp_status ws_get(acp_ctx* ctx, const char* name, size_t bytes, void** out) {
   if (bytes == 0) bytes = 8;
   auto it = ctx->ws.bufs.find(name);
@@ -36,6 +45,8 @@ acp_status ws_get(acp_ctx* ctx, const char* name, size_t bytes, void** out) {
     *out = it->second.first;
     return ACP_OK;
   }
+  // cudaFree synchronises the device, which must not overlap another thread's stream capture
+  std::lock_guard<std::mutex> lock(device_mutex());
   if (it != ctx->ws.bufs.end()) {
     cudaFree(it->second.first);  // synchronises the device before the memory is reused
     ctx->ws.bufs.erase(it);
@@ -358,6 +369,43 @@ acp_status acp_dynamical_matrix(acp_ctx* ctx, const acp_atoms* atoms, const doub
     return set_error(ctx, ACP_E_NOCONV, "some Sternheimer solves hit the iteration cap (max rel. res %.3e)",
                      rep.max_rel_res);
   return st;
+}
+
+acp_status acp_batch_dynamical_matrix(acp_ctx* const* ctxs, int n_sys, const acp_atoms* atoms,
+                                      const double* const* rho_d, double* const* D_h, acp_stats* stats,
+                                      acp_status* status_out, int n_workers) {
+  if (!ctxs || n_sys < 0 || !atoms || !rho_d || !D_h) return ACP_E_ARG;
+  for (int i = 0; i < n_sys; ++i)
+    if (!ctxs[i]) return ACP_E_ARG;
+  if (n_sys == 0) return ACP_OK;
+  int workers = n_workers > 0 ? n_workers : (int)std::thread::hardware_concurrency();
+  if (workers < 1) workers = 1;
+  if (workers > n_sys) workers = n_sys;
+  if (workers > 64) workers = 64;
+  std::vector<acp_status> st(n_sys, ACP_OK);
+  std::atomic<int> next{0};
+  // work queue over systems, largest first (the callers' order is kept in the outputs)
+  std::vector<int> order(n_sys);
+  for (int i = 0; i < n_sys; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctxs[a]->N > ctxs[b]->N; });
+  auto worker = [&]() {
+    for (;;) {
+      const int q = next.fetch_add(1);
+      if (q >= n_sys) return;
+      const int i = order[q];
+      st[i] = acp_dynamical_matrix(ctxs[i], &atoms[i], rho_d[i], D_h[i], nullptr, stats ? &stats[i] : nullptr);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < workers; ++w) pool.emplace_back(worker);
+  worker();
+  for (auto& t : pool) t.join();
+  acp_status worst = ACP_OK;
+  for (int i = 0; i < n_sys; ++i) {
+    if (status_out) status_out[i] = st[i];
+    if (worst == ACP_OK && st[i] != ACP_OK) worst = st[i];
+  }
+  return worst;
 }
 
 acp_status acp_phonons(acp_ctx* ctx, const double* D_h, int n, double* omega_h, double* modes_h) {

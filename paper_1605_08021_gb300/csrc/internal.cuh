@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -81,6 +82,7 @@ struct acp_ctx {
   bool tables32_stale = true;     // FP32 copies of the kinetic symbol, V_eff and twiddles
   std::map<long long, std::pair<int, int>> tc_tune;  // projector tile choice per shape
   bool mixed_refine = true;       // mixed precision: refine the multi-shift solves to stern_tol
+  long long graph_launch_nodes = 0;  // kernels replayed through CUDA graphs (launch counter)
   acp::FftPlan plan;
   acp::Workspace ws;
   acp::Profiler prof;
@@ -114,6 +116,10 @@ acp_status set_error(acp_ctx* ctx, acp_status st, const char* fmt, ...);
     if (s_ != ACP_OK) return s_;                                                               \
   } while (0)
 
+// Serialises the calls that may synchronise the device (workspace cudaMalloc / cudaFree, function
+// attributes) with CUDA-graph captures, when several host threads drive contexts at once.
+std::mutex& device_mutex();
+
 // Device buffer from the context's workspace, grown (never shrunk) to hold `bytes`.
 acp_status ws_get(acp_ctx* ctx, const char* name, size_t bytes, void** out);
 template <class T>
@@ -142,8 +148,10 @@ enum SpectralMult { MULT_KINETIC = 0, MULT_KHAT = 1, MULT_KHAT_INV = 2 };
 acp_status spectral_apply(acp_ctx* ctx, const double* X, int ldx, int ncol, SpectralMult mult, bool with_v,
                           const double* shift_d, double* Y, int ldy, double* alpha_d, const int* active_d,
                           const double* Xprev = nullptr, const double* beta_d = nullptr);
-// Raise the dynamic shared-memory limit of the spectral kernels (once per context).
+// Raise the dynamic shared-memory limit of the spectral kernels (once per device, never lowered).
 acp_status spectral_configure(acp_ctx* ctx);
+// Set the dynamic shared-memory limit of a kernel to the opt-in maximum minus its static usage.
+acp_status raise_smem_limit(acp_ctx* ctx, const void* func);
 // Perturbation potentials of n_atoms atoms (1D): G, B, d2V (each nullable, N x n_atoms).
 acp_status perturbations_1d(acp_ctx* ctx, int n_atoms, const double* R_d, const double* Z_d, const double* sig_d,
                             double* G, double* B, double* D2);
@@ -192,8 +200,11 @@ acp_status minres_batched_mixed(acp_ctx* ctx, const double* B, int ncol, const d
 acp_status minres_multishift_mixed(acp_ctx* ctx, const double* B, int nmu, const double* nodes_d, int nc, double* X,
                                    SolveReport* rep, double t0_ms);
 // spectral32.cu: FP32 (H - s) X, or the Lanczos form when Xprev is given (see spectral_apply).
+// With kdev (stored basis), X and Xprev are slot 0 of the basis and the kernel uses slots k and
+// k - 1, k = *kdev, slot stride kstride elements.
 acp_status spectral32_apply(acp_ctx* ctx, const float* X, int ldx, int ncol, const float* shift_d, float* Y, int ldy,
-                            float* alpha_d, const int* active_d, const float* Xprev, int ldp, const float* beta_d);
+                            float* alpha_d, const int* active_d, const float* Xprev, int ldp, const float* beta_d,
+                            const int* kdev = nullptr, long long kstride = 0);
 
 // tc_gemm.cu: FP32 projector Y = Q X on the tensor cores (3xTF32 tcgen05 GEMMs); X, Y FP32 blocks
 // with leading dimensions that are multiples of 4 (Y may alias X).  mixed_prepare builds the FP32

@@ -297,9 +297,11 @@ __global__ void __launch_bounds__(kThreads) msb32_init_kernel(int N, int nc, con
   }
 }
 
-__global__ void __launch_bounds__(kThreads) msb32_step_kernel(int N, int nc, int k, MsB32 s, double tol) {
+__global__ void __launch_bounds__(kThreads) msb32_step_kernel(int N, int nc, const int* __restrict__ kdev, MsB32 s,
+                                                              double tol) {
   __shared__ float red[32];
   __shared__ int any_active;
+  const int k = *kdev;  // step index from device memory, so that captured steps can be replayed
   const int mu = blockIdx.x;
   if (!s.active[mu]) return;
   const float* P = s.P + (size_t)mu * s.ld;
@@ -342,6 +344,8 @@ __global__ void __launch_bounds__(kThreads) msb32_step_kernel(int N, int nc, int
     if (!any_active || !isfinite(bn) || bn == 0.0 || it >= s.kmax) s.active[mu] = 0;
   }
 }
+
+__global__ void advance_k_kernel(int* kdev) { *kdev += 1; }
 
 __global__ void msb32_backsub_kernel(int nmu, int nc, MsB32 s) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -454,6 +458,57 @@ acp_status sum_iters(acp_ctx* ctx, const int* iters, int n, long long* steps, lo
   return ACP_OK;
 }
 
+// ---- CUDA-graph replay of the Lanczos loops ------------------------------------------------------
+constexpr int kChunk = 16;  // steps between convergence checks
+
+struct ChunkGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long nodes = 0;
+  ~ChunkGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+// Runs n Lanczos steps starting at step it0.  With `graphs`, a full chunk is captured once into a
+// CUDA graph (the step functions launch the same kernels with the same arguments in every chunk:
+// step indices live in device memory) and replayed for every later chunk; the first chunk always
+// runs eagerly, so that one-time work (tile autotuning, workspace growth) happens outside capture.
+template <class Step>
+acp_status run_chunk(acp_ctx* ctx, ChunkGraph& g, bool graphs, int it0, int n, Step step) {
+  if (!graphs || n != kChunk || it0 == 0) {
+    for (int i = 0; i < n; ++i) ACP_TRY(step(it0 + i));
+    return ACP_OK;
+  }
+  if (!g.exec) {
+    std::lock_guard<std::mutex> lock(device_mutex());
+    const bool prof_on = ctx->prof.on;
+    ctx->prof.on = false;
+    const long long l0 = ctx->prof.launches;
+    ACP_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    acp_status st = ACP_OK;
+    for (int i = 0; i < n && st == ACP_OK; ++i) st = step(it0 + i);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    ctx->prof.on = prof_on;
+    g.nodes = ctx->prof.launches - l0;
+    ctx->prof.launches = l0;
+    if (st != ACP_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return st != ACP_OK ? st : set_error(ctx, ACP_E_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      g.exec = nullptr;
+      return set_error(ctx, ACP_E_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+    }
+  }
+  ACP_CUDA(ctx, cudaGraphLaunch(g.exec, ctx->stream));
+  ctx->prof.launches += g.nodes;
+  return ACP_OK;
+}
+
 // FP32 inner solve of Q(H - s_j)Q D_j = R32_j (R32 projected, unit or zero columns).
 acp_status minres32(acp_ctx* ctx, const float* R32, int ncol, const float* shift32, float* D32, double tol,
                     const double* tolc, long long* steps, long long* max_it, double t0_ms) {
@@ -480,18 +535,24 @@ acp_status minres32(acp_ctx* ctx, const float* R32, int ncol, const float* shift
   ACP_LAUNCH(ctx);
   const int maxit = ctx->opt.stern_maxit;
   const int period = projection_period(ctx);
-  for (int it = 0; it < maxit; ++it) {
+  auto step = [&](int it) -> acp_status {
     ACP_TRY(spectral32_apply(ctx, s.V, ld, ncol, shift32, s.P, ld, s.alpha, s.active, s.Vp, ld, s.beta));
     if (it % period == period - 1 || it < 2) ACP_TRY(project32(ctx, s.P, ld, ncol, s.P, ld));
     ::acp::note_launch(ctx);
     m32_step_kernel<<<ncol, kThreads, 0, ctx->stream>>>(N, s, D32, tol, maxit);
     ACP_LAUNCH(ctx);
-    if ((it & 15) == 15 || it == maxit - 1) {
-      int n_act = 0;
-      ACP_TRY(count32(ctx, s.active, ncol, &n_act));
-      if (n_act == 0) break;
-      if (deadline_passed(ctx, t0_ms)) return set_error(ctx, ACP_E_TIMEOUT, "deadline passed in FP32 MINRES");
-    }
+    return ACP_OK;
+  };
+  ChunkGraph graph;
+  const bool graphs = ctx->opt.use_graphs && period == 1 && ctx->stream != nullptr;
+  for (int it = 0; it < maxit;) {
+    const int n = (maxit - it < kChunk) ? maxit - it : kChunk;
+    ACP_TRY(run_chunk(ctx, graph, graphs, it, n, step));
+    it += n;
+    int n_act = 0;
+    ACP_TRY(count32(ctx, s.active, ncol, &n_act));
+    if (n_act == 0) break;
+    if (deadline_passed(ctx, t0_ms)) return set_error(ctx, ACP_E_TIMEOUT, "deadline passed in FP32 MINRES");
   }
   ACP_TRY(tc_check(ctx));
   return sum_iters(ctx, s.iters, ncol, steps, max_it);
@@ -643,21 +704,34 @@ acp_status minres_multishift_mixed(acp_ctx* ctx, const double* B, int nmu, const
   msb32_init_kernel<<<nmu, kThreads, 0, ctx->stream>>>(N, nc, B32, s);
   ACP_LAUNCH(ctx);
   const int period = projection_period(ctx);
-  for (int k = 1; k <= kmax; ++k) {
-    const float* vk = s.Vb + (size_t)k * ld;
-    const float* vkm = s.Vb + (size_t)(k - 1) * ld;
-    ACP_TRY(spectral32_apply(ctx, vk, (int)s.slot_ld, nmu, nullptr, s.P, ld, s.alpha, s.active, vkm, (int)s.slot_ld,
-                             s.beta));
-    if ((k - 1) % period == period - 1 || k <= 2) ACP_TRY(project32(ctx, s.P, ld, nmu, s.P, ld));
+  int* kdev = nullptr;
+  ACP_TRY(ws(ctx, "ms32_k", 1, &kdev));
+  {
+    const int one = 1;
+    ACP_CUDA(ctx, cudaMemcpyAsync(kdev, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  auto step = [&](int k0) -> acp_status {  // k0: 0-based step; the basis slot k = k0 + 1 is on the device
+    ACP_TRY(spectral32_apply(ctx, s.Vb, (int)s.slot_ld, nmu, nullptr, s.P, ld, s.alpha, s.active, s.Vb,
+                             (int)s.slot_ld, s.beta, kdev, ld));
+    if (k0 % period == period - 1 || k0 < 2) ACP_TRY(project32(ctx, s.P, ld, nmu, s.P, ld));
     ::acp::note_launch(ctx);
-    msb32_step_kernel<<<nmu, kThreads, 0, ctx->stream>>>(N, nc, k, s, kInnerTol);
+    msb32_step_kernel<<<nmu, kThreads, 0, ctx->stream>>>(N, nc, kdev, s, kInnerTol);
     ACP_LAUNCH(ctx);
-    if ((k & 15) == 0 || k == kmax) {
-      int n_act = 0;
-      ACP_TRY(count32(ctx, s.active, nmu, &n_act));
-      if (n_act == 0) break;
-      if (deadline_passed(ctx, t0_ms)) return set_error(ctx, ACP_E_TIMEOUT, "deadline passed in FP32 MINRES");
-    }
+    ::acp::note_launch(ctx);
+    advance_k_kernel<<<1, 1, 0, ctx->stream>>>(kdev);
+    ACP_LAUNCH(ctx);
+    return ACP_OK;
+  };
+  ChunkGraph graph;
+  const bool graphs = ctx->opt.use_graphs && period == 1 && ctx->stream != nullptr;
+  for (int k0 = 0; k0 < kmax;) {
+    const int n = (kmax - k0 < kChunk) ? kmax - k0 : kChunk;
+    ACP_TRY(run_chunk(ctx, graph, graphs, k0, n, step));
+    k0 += n;
+    int n_act = 0;
+    ACP_TRY(count32(ctx, s.active, nmu, &n_act));
+    if (n_act == 0) break;
+    if (deadline_passed(ctx, t0_ms)) return set_error(ctx, ACP_E_TIMEOUT, "deadline passed in FP32 MINRES");
   }
   ACP_TRY(tc_check(ctx));
   ::acp::note_launch(ctx);

@@ -264,10 +264,26 @@ __global__ void __launch_bounds__(kMaxThreads) perturbation_kernel(PlanArg plan,
 
 }  // namespace
 
+// The dynamic shared-memory limit is a property of the kernel, shared by every context in the
+// process: it is raised once to the device's opt-in maximum (a context with a smaller grid must
+// not lower it under another context's feet); occupancy follows the size of each launch.
 acp_status spectral_configure(acp_ctx* ctx) {
-  const int bytes = ctx->N * (int)sizeof(double2);
-  ACP_CUDA(ctx, cudaFuncSetAttribute(spectral_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  ACP_CUDA(ctx, cudaFuncSetAttribute(perturbation_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  std::lock_guard<std::mutex> lock(device_mutex());
+  static int configured_device = -1;
+  if (configured_device == ctx->device) return ACP_OK;
+  ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(spectral_kernel)));
+  ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(perturbation_kernel)));
+  configured_device = ctx->device;
+  return ACP_OK;
+}
+
+// Dynamic shared-memory limit of `func` = the device's opt-in maximum minus its static shared memory.
+acp_status raise_smem_limit(acp_ctx* ctx, const void* func) {
+  int optin = 0;
+  ACP_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+  cudaFuncAttributes fa{};
+  ACP_CUDA(ctx, cudaFuncGetAttributes(&fa, func));
+  ACP_CUDA(ctx, cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
   return ACP_OK;
 }
 

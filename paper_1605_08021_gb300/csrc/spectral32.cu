@@ -154,9 +154,17 @@ __global__ void __launch_bounds__(kMaxThreads)
     spectral32_kernel(const float* __restrict__ X, int ldx, int ncol, PlanArgF plan, const float2* __restrict__ tw,
                       const float* __restrict__ kin, const float* __restrict__ V, const float* __restrict__ shift,
                       float* __restrict__ Y, int ldy, float* __restrict__ alpha, const int* __restrict__ active,
-                      const float* __restrict__ Xp, int ldp, const float* __restrict__ beta) {
+                      const float* __restrict__ Xp, int ldp, const float* __restrict__ beta,
+                      const int* __restrict__ kdev, long long kstride) {
   extern __shared__ float2 sbuf32[];
   __shared__ float red[32];
+  if (kdev) {
+    // stored Lanczos basis: x = slot k, x_prev = slot k - 1, with k read from device memory so
+    // that a captured sequence of steps can be replayed
+    const long long k = *kdev;
+    X += k * kstride;
+    Xp += (k - 1) * kstride;
+  }
   const int c0 = 2 * blockIdx.x, c1 = c0 + 1;
   const bool act0 = (active == nullptr) || active[c0] != 0;
   const bool act1 = (c1 < ncol) && ((active == nullptr) || active[c1] != 0);
@@ -235,8 +243,14 @@ acp_status tables32(acp_ctx* ctx, const float** kin32, const float** V32, const 
     tables32_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ctx->d_kin, ctx->d_V, ctx->d_tw, buf, buf + N,
                                                              reinterpret_cast<float2*>(buf + 2 * N));
     ACP_LAUNCH(ctx);
-    ACP_CUDA(ctx, cudaFuncSetAttribute(spectral32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       N * (int)sizeof(float2)));
+    // raised once per device to the opt-in maximum, never lowered (the limit is shared by all
+    // contexts; occupancy follows the size of each launch)
+    std::lock_guard<std::mutex> lock(device_mutex());
+    static int configured_device = -1;
+    if (configured_device != ctx->device) {
+      ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(spectral32_kernel)));
+      configured_device = ctx->device;
+    }
     ctx->tables32_stale = false;
   }
   *kin32 = buf;
@@ -246,7 +260,8 @@ acp_status tables32(acp_ctx* ctx, const float** kin32, const float** V32, const 
 }
 
 acp_status spectral32_apply(acp_ctx* ctx, const float* X, int ldx, int ncol, const float* shift_d, float* Y, int ldy,
-                            float* alpha_d, const int* active_d, const float* Xprev, int ldp, const float* beta_d) {
+                            float* alpha_d, const int* active_d, const float* Xprev, int ldp, const float* beta_d,
+                            const int* kdev, long long kstride) {
   if (ncol <= 0) return ACP_OK;
   const float *kin = nullptr, *V = nullptr;
   const float2* tw = nullptr;
@@ -259,7 +274,7 @@ acp_status spectral32_apply(acp_ctx* ctx, const float* X, int ldx, int ncol, con
   ::acp::note_launch(ctx);
   cudaEvent_t ev0 = prof_begin(ctx);
   spectral32_kernel<<<blocks, ctx->plan.threads, ctx->N * sizeof(float2), ctx->stream>>>(
-      X, ldx, ncol, pa, tw, kin, V, shift_d, Y, ldy, alpha_d, active_d, Xprev, ldp, beta_d);
+      X, ldx, ncol, pa, tw, kin, V, shift_d, Y, ldy, alpha_d, active_d, Xprev, ldp, beta_d, kdev, kstride);
   ACP_LAUNCH(ctx);
   const double lg = std::log2((double)ctx->N);
   const double flops = 2.0 * 5.0 * ctx->N * lg * blocks + 6.0 * (double)ctx->N * ncol;

@@ -19,6 +19,8 @@
 
 #include <cudaTypedefs.h>
 
+#include <atomic>
+
 namespace acp {
 
 namespace {
@@ -252,16 +254,15 @@ __global__ void psi_split_kernel(int N, int no, int ld32, int no_pad, const doub
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q{};
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    else
-      cudaGetLastError();
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -293,11 +294,12 @@ size_t smem_for(int bn) { return (size_t)kStages * (2 * kBM * kBK * 4 + 2 * (siz
 
 acp_status launch_tc3(acp_ctx* ctx, dim3 grid, const CUtensorMap& a, const CUtensorMap& alo, const CUtensorMap& bhi,
                       const CUtensorMap& blo, const TcArgs& p) {
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<bool> configured{false};
+  if (!configured.load()) {
+    std::lock_guard<std::mutex> lock(device_mutex());
     ACP_CUDA(ctx, cudaFuncSetAttribute(tc3_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem_for(256)));
-    configured = true;
+    configured.store(true);
   }
   ::acp::note_launch(ctx);
   tc3_gemm_kernel<<<grid, kThreads, smem_for(p.BN), ctx->stream>>>(a, alo, bhi, blo, p);

@@ -144,3 +144,14 @@ def test_multishift_storage_variants_agree():
     Uv, sv = context(name, ms_variant=2, **kw).apply_chi0(to_gpu(G))
     assert rel(to_np(Ub), to_np(Uv)) < 1e-11
     assert sb["rhs_solved"] == sv["rhs_solved"]
+
+
+def test_contexts_of_different_grids_coexist():
+    """The shared-memory limit of the spectral kernels is process-wide: a context on a small grid
+    created after one on a large grid must not lower it below what the large grid needs."""
+    m = model("c2")
+    big = context("c2")
+    small = context("small3_96_2")
+    X = np.random.default_rng(7).standard_normal((m.N, 3))
+    assert rel(to_np(big.hamiltonian_apply(to_gpu(X))), m.apply_H(X)) < 1e-12
+    del small
