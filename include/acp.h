@@ -170,9 +170,11 @@ acp_status acp_dynamical_matrix(acp_ctx* ctx, const acp_atoms* atoms, const doub
    different systems overlap on their streams, and with use_graphs set in the contexts' options
    every 16-step chunk of the FP32 Lanczos loops is one CUDA graph launch.  atoms[i], rho_d[i],
    D_h[i] and stats[i] (nullable) are system i's arguments of acp_dynamical_matrix;
-   status_out (nullable, n_sys entries) receives each system's status.  Returns ACP_OK, or the
-   first failing system's status (the others still run).  No counterpart in the paper, which
-   treats one system at a time. */
+   status_out (nullable, n_sys entries) receives each system's status.  Each context's device
+   workspace is released when its system is done (so the batch holds memory only for the
+   systems in flight; it regrows on the context's next call).  Returns ACP_OK, or the first
+   failing system's status (the others still run).  No counterpart in the paper, which treats
+   one system at a time. */
 acp_status acp_batch_dynamical_matrix(acp_ctx* const* ctxs, int n_sys, const acp_atoms* atoms,
                                       const double* const* rho_d, double* const* D_h, acp_stats* stats,
                                       acp_status* status_out, int n_workers);

@@ -394,6 +394,15 @@ acp_status acp_batch_dynamical_matrix(acp_ctx* const* ctxs, int n_sys, const acp
       if (q >= n_sys) return;
       const int i = order[q];
       st[i] = acp_dynamical_matrix(ctxs[i], &atoms[i], rho_d[i], D_h[i], nullptr, stats ? &stats[i] : nullptr);
+      // hand the system's workspace back, so that the device memory of the batch is bounded by
+      // the systems in flight rather than by all of them (it regrows on the context's next call)
+      cudaStreamSynchronize(ctxs[i]->stream);
+      std::lock_guard<std::mutex> lock(device_mutex());
+      for (auto& kv : ctxs[i]->ws.bufs)
+        if (kv.second.first) cudaFree(kv.second.first);
+      ctxs[i]->ws.bufs.clear();
+      ctxs[i]->psi32_stale = true;
+      ctxs[i]->tables32_stale = true;
     }
   };
   std::vector<std::thread> pool;
