@@ -167,5 +167,115 @@ def scf(sysm: System, tol: float = 1e-11, maxit: int = 200, beta: float = 0.3, h
     return gs
 
 
+def _grid_2d(sysm: System):
+    nx, ny = sysm.n
+    Lx, Ly = sysm.L
+    kx = 2.0 * np.pi * np.fft.fftfreq(nx, d=1.0 / nx) / Lx
+    ky = 2.0 * np.pi * np.fft.fftfreq(ny, d=1.0 / ny) / Ly
+    KX, KY = np.meshgrid(kx, ky)
+    return KX, KY, KX ** 2 + KY ** 2
+
+
+def _lowest_2d(sysm: System, V: np.ndarray, k2: np.ndarray, count: int, dense_limit: int = 4096):
+    """Lowest `count` eigenpairs of H = -1/2 Laplacian + V on the 2D grid (x fastest)."""
+    nx, ny = sysm.n
+    N = nx * ny
+    if N <= dense_limit:
+        def circ(n, L):
+            k = 2.0 * np.pi * np.fft.fftfreq(n, d=1.0 / n) / L
+            t = np.real(np.fft.ifft(0.5 * k ** 2))
+            idx = (np.arange(n)[:, None] - np.arange(n)[None, :]) % n
+            return t[idx]
+        T = np.kron(np.eye(ny), circ(nx, sysm.L[0])) + np.kron(circ(ny, sysm.L[1]), np.eye(nx))
+        return sla.eigh(T + np.diag(V), subset_by_index=[0, count - 1], driver="evr")
+    import scipy.sparse.linalg as spla
+    half_k2 = 0.5 * k2
+
+    def mv(x):
+        X = x.reshape(ny, nx, -1) if x.ndim > 1 else x.reshape(ny, nx)
+        if X.ndim == 3:
+            Y = np.real(np.fft.ifft2(half_k2[:, :, None] * np.fft.fft2(X, axes=(0, 1)), axes=(0, 1)))
+            return Y.reshape(N, -1) + V[:, None] * x.reshape(N, -1)
+        return np.real(np.fft.ifft2(half_k2 * np.fft.fft2(X))).reshape(N) + V * x.reshape(N)
+    op = spla.LinearOperator((N, N), matvec=mv, matmat=mv, dtype=np.float64)
+    w, U = spla.eigsh(op, k=count, which="SA", tol=1e-14, ncv=min(N, 2 * count + 40),
+                      v0=np.ones(N) / np.sqrt(N))
+    order = np.argsort(w)
+    return w[order], U[:, order]
+
+
+def scf_2d(sysm: System, tol: float = 1e-9, maxit: int = 100, beta: float = 0.3, history: int = 12,
+           n_extra: int = 4, use_cache: bool = True, verbose: bool = False) -> GroundState:
+    """Anderson-mixed SCF for the 2D model; returns exact eigenpairs of H[V] for the final V.
+
+    Dense eigensolver for small grids, Lanczos (ARPACK, FFT matrix-vector products, tolerance
+    1e-14) for large ones."""
+    t0 = time.time()
+    nx, ny = sysm.n
+    N = nx * ny
+    dV = sysm.dV
+    n_orb, f = sysm.n_orb, sysm.occ
+    KX, KY, k2 = _grid_2d(sysm)
+    khat = 4.0 * np.pi * sysm.scale / (k2 + sysm.kappa ** 2)
+    F = np.zeros((ny, nx), dtype=np.complex128)
+    G0 = np.zeros((ny, nx), dtype=np.complex128)
+    for (Rx, Ry), ZI, sI in zip(sysm.R, sysm.Z, sysm.sigma):
+        ph = np.exp(-1j * (KX * Rx + KY * Ry))
+        F += -ZI * np.exp(-0.5 * sI ** 2 * k2) * ph
+        G0 += ZI * np.exp(-0.5 * 1.5 ** 2 * k2) * ph
+    m = np.real(np.fft.ifft2(F)).reshape(N) / dV
+
+    def potential(rho):
+        c = np.fft.fft2((rho + m).reshape(ny, nx))
+        c[0, 0] = 0.0
+        return np.real(np.fft.ifft2(khat * c)).reshape(N)
+
+    def solve(V):
+        w, U = _lowest_2d(sysm, V, k2, n_orb + n_extra)
+        psi = U[:, :n_orb] / np.sqrt(dV)
+        return w, psi, f * np.sum(psi ** 2, axis=1)
+
+    cache_file = os.path.join(CACHE_DIR, sysm.key() + ".npy")
+    if use_cache and os.path.exists(cache_file):
+        V = np.load(cache_file)
+        w, psi, rho = solve(V)
+        res = np.linalg.norm(potential(rho) - V) / max(np.linalg.norm(V), 1e-300)
+        if res < max(1e-7, 100.0 * tol):
+            return GroundState(V=V, psi=np.asfortranarray(psi), eps=w, rho=rho, m=m, n_orb=n_orb,
+                               scf_residual=float(res), iterations=0, seconds=time.time() - t0)
+    rho = np.real(np.fft.ifft2(G0)).reshape(N) / dV
+    X, Rr = [], []
+    err = np.inf
+    it = 0
+    for it in range(maxit):
+        V = potential(rho)
+        w, psi, rho_out = solve(V)
+        res = rho_out - rho
+        err = float(np.linalg.norm(res) * np.sqrt(dV) / sysm.n_elec)
+        if verbose:
+            print(f"scf2d {it:3d} residual {err:.3e} gap {w[n_orb] - w[n_orb - 1]:.6f}", flush=True)
+        if err < tol:
+            break
+        X.append(rho.copy())
+        Rr.append(res.copy())
+        X, Rr = X[-history:], Rr[-history:]
+        if len(X) > 1:
+            dR = np.array([Rr[i + 1] - Rr[i] for i in range(len(Rr) - 1)]).T
+            dX = np.array([X[i + 1] - X[i] for i in range(len(X) - 1)]).T
+            gam = np.linalg.lstsq(dR, res, rcond=1e-12)[0]
+            rho = rho - dX @ gam + beta * (res - dR @ gam)
+        else:
+            rho = rho + beta * res
+    gs = GroundState(V=V, psi=np.asfortranarray(psi), eps=w, rho=rho_out, m=m, n_orb=n_orb,
+                     scf_residual=err, iterations=it + 1, seconds=time.time() - t0)
+    if use_cache and err < tol:
+        os.makedirs(CACHE_DIR, exist_ok=True)
+        np.save(cache_file, V)
+    return gs
+
+
 def ground_state(sysm: System, **kw) -> GroundState:
+    if sysm.dim == 2:
+        kw.pop("initial", None)
+        return scf_2d(sysm, **kw)
     return scf(sysm, **kw)

@@ -131,6 +131,12 @@ def config(index: int) -> System:
         R = ((np.arange(128) + 0.5) * 10.0 + disp).reshape(128, 1)
         return System(name="chain128_mixed", dim=1, n=(5120,), L=(1280.0,), R=R, Z=Z,
                       sigma=np.ones(128), mass=np.ones(128), kappa=0.01, scale=0.5, occ=1)
+    if index == 3:
+        # 8 x 8 square lattice, spacing 10 bohr, one vacancy (drawn), Z = 2, sigma = 1.2,
+        # kappa = 0.01, grid 160 x 160 (h = 0.5), occupation 2: 63 atoms, 63 orbitals, 126 perturbations
+        rng = _rng(3)
+        vac = int(rng.integers(0, 64))
+        return lattice_2d("lattice8x8_vac", 8, 8, 10.0, 2.0, 1.2, 0.01, 1.0, 160, occ=2, vacancies=(vac,))
     raise ValueError(f"configuration {index} is not available")
 
 
@@ -167,6 +173,33 @@ def batch_config(index: int = 4, n_sys: int = 64, min_atoms: int = 16, max_atoms
         out.append(System(name=f"batch{index}_{k}_na{n_atoms}", dim=1, n=(n_grid,), L=(10.0 * n_atoms,), R=R, Z=Z,
                           sigma=np.ones(n_atoms), mass=np.ones(n_atoms), kappa=0.01, scale=scale, occ=1))
     return out
+
+
+def lattice_2d(name, nxa, nya, spacing, Z, sigma, kappa, scale, n_grid, occ, vacancies=(), displacement=0.0,
+               rng=None, mass=1.0) -> System:
+    """Periodic square lattice of nxa x nya sites at ((i + 1/2), (j + 1/2)) * spacing, optional
+    vacancies (site indices i + nxa j) and uniform displacements per coordinate; grid n_grid^2."""
+    sites = [(i, j) for j in range(nya) for i in range(nxa) if i + nxa * j not in set(vacancies)]
+    R = (np.array(sites, dtype=np.float64) + 0.5) * spacing
+    if displacement:
+        R = R + rng.uniform(-displacement, displacement, R.shape)
+    n_atoms = R.shape[0]
+    Zv = np.broadcast_to(np.asarray(Z, dtype=np.float64), (n_atoms,)).copy()
+    return System(name=name, dim=2, n=(int(n_grid), int(n_grid)), L=(nxa * spacing, nya * spacing), R=R, Z=Zv,
+                  sigma=np.full(n_atoms, float(sigma)), mass=np.full(n_atoms, float(mass)), kappa=float(kappa),
+                  scale=float(scale), occ=int(occ))
+
+
+def small_lattice(nxa=2, nya=2, n_grid=32, seed=0, spacing=8.0, occ=1, scale=1.0, mixed=True,
+                  displacement=0.3, sigma=1.2) -> System:
+    """Small 2D lattices for parity tests (dense eigensolvers and dense chi0 stay cheap)."""
+    rng = _rng(91, seed)
+    n = nxa * nya
+    Z = rng.integers(1, 3, n).astype(np.float64) if mixed else np.full(n, 2.0)
+    if occ == 2 and int(Z.sum()) % 2:
+        Z[0] = 3.0 - Z[0]
+    return lattice_2d(f"lat{nxa}x{nya}_{n_grid}_s{seed}", nxa, nya, spacing, Z, sigma, 0.01, scale, n_grid, occ,
+                      displacement=displacement, rng=rng)
 
 
 def mixed_chain(n_atoms: int, n_grid: int, seed: int = 0, scale: float = 0.5) -> System:

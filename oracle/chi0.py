@@ -59,10 +59,13 @@ def chi0_apply(model, G, tol=1e-12, maxit=5000, chunk=2048, return_info=False):
 
 def full_spectrum(model):
     """All eigenpairs of the grid Hamiltonian (dense), eigenvectors normalised with weight h."""
-    N = model.N
-    t = np.real(np.fft.ifft(0.5 * model.k ** 2))
-    idx = (np.arange(N)[:, None] - np.arange(N)[None, :]) % N
-    H = t[idx] + np.diag(model.V)
+    if hasattr(model, "dense_H"):
+        H = model.dense_H()
+    else:
+        N = model.N
+        t = np.real(np.fft.ifft(0.5 * model.k ** 2))
+        idx = (np.arange(N)[:, None] - np.arange(N)[None, :]) % N
+        H = t[idx] + np.diag(model.V)
     w, U = np.linalg.eigh(H)
     return w, U / np.sqrt(model.h)
 

@@ -14,11 +14,18 @@ import numpy as np
 
 def dynamical_matrix(model, U, symmetrize=True):
     G, _ = model.perturbations()
-    D2 = model.second_derivatives()
     Hm = (G.T @ U) * model.h
-    Hm = Hm + np.diag(D2.T @ model.rho * model.h)
+    if model.sys.dim == 1:
+        D2 = model.second_derivatives()
+        Hm = Hm + np.diag(D2.T @ model.rho * model.h)
+    else:
+        # delta_IJ int rho d^2 V_I / dR_Ia dR_Ib: one d x d block per atom
+        blk = np.einsum("r,rIab->Iab", model.rho, model.second_derivative_blocks()) * model.h
+        d = model.sys.dim
+        for I in range(model.sys.n_atoms):
+            Hm[d * I:d * I + d, d * I:d * I + d] += blk[I]
     Hm = Hm + model.ion_hessian()
-    mass = model.sys.mass
+    mass = np.repeat(model.sys.mass, model.sys.dim)
     D = Hm / np.sqrt(np.outer(mass, mass))
     asym = np.linalg.norm(D - D.T) / max(np.linalg.norm(D), 1e-300)
     if symmetrize:

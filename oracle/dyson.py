@@ -18,6 +18,9 @@ from .chi0 import chi0_apply, chi0_matrix_sos
 def kernel_matrix(model):
     """Dense matrix of the periodic convolution with K acting on grid values."""
     N = model.N
+    if model.sys.dim == 2:
+        # column j = K applied to the unit vector e_j, spectrally
+        return model.apply_K(np.eye(N))
     kc = np.real(np.fft.ifft(model.khat))
     idx = (np.arange(N)[:, None] - np.arange(N)[None, :]) % N
     return kc[idx]
