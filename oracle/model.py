@@ -167,12 +167,17 @@ class Model2D:
     Khat(k) = 4 pi s / (|k|^2 + kappa^2), whose periodic real-space form is the image sum of
     2 s K0(kappa r); m_I(r) = -Z_I exp(-|r - R_I|^2 / 2 sigma^2) / (2 pi sigma^2), Fourier
     coefficient -Z_I exp(-sigma^2 |k|^2 / 2) exp(-i k.R_I).  Perturbation columns are ordered
-    p = 2 I + a (a = 0: x, 1: y), the index of D_{Ia,Jb}.
+    p = 2 I + a (a = 0: x, 1: y), the index of D_{Ia,Jb}.  The image sums of E_II run over
+    |n| <= images per axis (default: enough shells for exp(-kappa r) < exp(-40)).
     """
 
-    def __init__(self, sysm, gs=None, images=60):
+    def __init__(self, sysm, gs=None, images=None):
         if sysm.dim != 2:
             raise ValueError("Model2D needs a 2D system")
+        # images of the periodic E_II sum: K0(kappa r) ~ exp(-kappa r), so shells out to
+        # r = 40 / kappa leave less than exp(-40) of the sum
+        if images is None:
+            images = max(2, int(np.ceil(40.0 / (sysm.kappa * min(sysm.L)))))
         self.sys = sysm
         self.nx, self.ny = sysm.n
         self.Lx, self.Ly = sysm.L
