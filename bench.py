@@ -39,6 +39,11 @@ ACP_PARAMS = dict(id_tol=1e-8, n_cheb=16, sketch_r=8, dyson_tol=1e-6, dyson_maxi
 
 def workload_name():
     form = "ACP FP64" if PRECISION == 0 else "ACP mixed precision"
+    if WORKLOAD == "c3":
+        return ("2D periodic rHF model: 8x8 square lattice (spacing 10 bohr) with one vacancy, 63 atoms, Z=2, "
+                f"sigma 1.2, kappa 0.01, grid 160x160, 63 orbitals (occupation 2), 126 perturbations; {form} "
+                f"(N_c={ACP_PARAMS['n_cheb']}, id_tol={ACP_PARAMS['id_tol']:g}, SRFT r={ACP_PARAMS['sketch_r']}, "
+                f"Alg. 4 delta={ACP_PARAMS['dyson_tol']:g})")
     if WORKLOAD == "chain64":
         return ("1D periodic rHF chain, 64 atoms (config-2 recipe at half size, N=2560) for profiler captures; "
                 f"{form} (N_c={ACP_PARAMS['n_cheb']}, id_tol={ACP_PARAMS['id_tol']:g})")
@@ -154,11 +159,20 @@ def build_inputs():
     import acp_workloads as W
     if WORKLOAD == "chain64":
         s = W.mixed_chain(64, 2560, seed=0)
+    elif WORKLOAD == "c3":
+        s = W.config(3)
     else:
         s = W.config(CONFIG)
     gs = W.ground_state(s)
-    om = W.srft_sketch(s.n_pert, ACP_PARAMS["sketch_r"], CONFIG)
+    om = W.srft_sketch(s.n_pert, ACP_PARAMS["sketch_r"], 3 if WORKLOAD == "c3" else CONFIG)
     return s, gs, om
+
+
+def grid_args(s):
+    """(n, L) of a Context and the atom coordinates as acp_atoms takes them."""
+    if s.dim == 2:
+        return s.n, s.L, s.R
+    return s.n[0], s.L[0], s.R[:, 0]
 
 
 PRECISION = 0
@@ -170,7 +184,8 @@ def make_context(P, s, gs, om, V, psi):
                   n_cheb=ACP_PARAMS["n_cheb"], dyson_tol=ACP_PARAMS["dyson_tol"],
                   dyson_maxit=ACP_PARAMS["dyson_maxit"], stern_tol=ACP_PARAMS["stern_tol"],
                   precision=PRECISION, use_graphs=USE_GRAPHS)
-    return P.Context(s.n[0], s.L[0], s.kappa, s.scale, V, psi, gs.eps[: gs.n_orb], o)
+    n, L, _ = grid_args(s)
+    return P.Context(n, L, s.kappa, s.scale, V, psi, gs.eps[: gs.n_orb], o)
 
 
 def run_gpu(args):
@@ -189,7 +204,7 @@ def run_gpu(args):
     V = torch.tensor(gs.V, dtype=torch.float64, device="cuda")
     psi = torch.tensor(np.ascontiguousarray(gs.psi.T), dtype=torch.float64, device="cuda")
     rho = torch.tensor(gs.rho, dtype=torch.float64, device="cuda")
-    R, Z, sig = s.R[:, 0].copy(), s.Z.copy(), s.sigma.copy()
+    R, Z, sig = grid_args(s)[2].copy(), s.Z.copy(), s.sigma.copy()
     ctx = make_context(P, s, gs, om, V, psi)
     stream = ctx.stream
 
@@ -247,7 +262,7 @@ def run_gpu(args):
     barrier(dist)
 
     comparison = None
-    if not args.no_compare and WORKLOAD == "c2" and rank == 0:
+    if not args.no_compare and WORKLOAD in ("c2", "c3") and rank == 0:
         comparison = compare_forms(P, s, gs, om, V, psi, rho, R, Z, sig)
 
     ms_max = max_over_ranks(dist, ms)
@@ -344,7 +359,8 @@ def compare_forms(P, s, gs, om, V, psi, rho, R, Z, sig):
         PRECISION = saved
     o = P.options(method=P.ACP_METHOD_PLAIN, occ=float(s.occ), stern_tol=ACP_PARAMS["stern_tol"],
                   dyson_tol=1e-10, dyson_maxit=80, precision=0)
-    ctxp = P.Context(s.n[0], s.L[0], s.kappa, s.scale, V, psi, gs.eps[: gs.n_orb], o)
+    n, L, _ = grid_args(s)
+    ctxp = P.Context(n, L, s.kappa, s.scale, V, psi, gs.eps[: gs.n_orb], o)
     G, _, _ = ctxp.perturbations(R, Z, sig)
     Gs = G[:4].contiguous()
     torch.cuda.synchronize()
@@ -543,9 +559,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the comparison with the other ACP arithmetic and with plain FP64 DFPT")
-    ap.add_argument("--workload", choices=["c2", "chain64", "c4"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "chain64", "c3", "c4"], default="c2",
                     help="c2: the benchmark configuration; chain64: half-size chain for profiler captures; "
-                         "c4: 64 chains of uneven size through the batched form")
+                         "c3: the 2D lattice; c4: 64 chains of uneven size through the batched form")
     ap.add_argument("--batch-workers", type=int, default=8, help="worker threads of the batched form (c4)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed",
                     help="arithmetic of the Sternheimer solves")
@@ -555,6 +571,9 @@ def main(argv=None):
     args = ap.parse_args(argv)
     global WORKLOAD, PRECISION, USE_GRAPHS
     USE_GRAPHS = 1 if args.graphs else 0
+    if args.workload == "c3":
+        # the paper's 2D settings: 30 Chebyshev nodes, SRFT factor 16 (Sec. 4.2)
+        ACP_PARAMS.update(n_cheb=30, sketch_r=16)
     WORKLOAD = args.workload
     PRECISION = 1 if args.precision == "mixed" else 0
     if args.impl == "reference":

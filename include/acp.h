@@ -54,7 +54,12 @@ enum { ACP_METHOD_PLAIN = 0, ACP_METHOD_ACP = 1 };
    compression, the Dyson update, D and its eigenvalues stay in FP64. */
 enum { ACP_PREC_FP64 = 0, ACP_PREC_MIXED = 1 };
 
-/* Periodic grid.  dim = 1 only; n[0] must factor into 2, 3 and 5 and lie in [8, 8192]. */
+/* Periodic grid.  dim = 1: n[0] points on [0, L[0]), n[0] = 2^a 3^b 5^c in [8, 8192] (and within
+   the thread budget of one CTA per transform).  dim = 2: n[0] x n[1] points on
+   [0, L[0]) x [0, L[1]), each n = 2^a 3^b 5^c in [8, 4096]; grid functions are flattened with x
+   fastest (index i + n[0] j), the quadrature weight is h = (L[0]/n[0]) (L[1]/n[1]), and the
+   2D forms of the kernel and pseudocharges apply (Sec. 4: K has symbol 4 pi s/(|k|^2+kappa^2),
+   m_I(r) = -Z_I exp(-|r-R_I|^2/2 sigma^2)/(2 pi sigma^2)). */
 typedef struct {
   int dim;
   int n[2];
@@ -69,8 +74,9 @@ typedef struct {
 } acp_kernel;
 
 /* Atoms with Gaussian pseudocharges m_I(x) = -Z_I exp(-(x-R_I)^2/2 sigma_I^2)/sqrt(2 pi sigma_I^2)
-   (Eq. pseudocharge, Sec. 4.1).  Host arrays of length n_atoms (R: n_atoms * dim); mass may be
-   NULL (all masses 1, so D is the Hessian). */
+   (Eq. pseudocharge, Sec. 4.1; the 2D form above).  Host arrays of length n_atoms (R: n_atoms *
+   dim, the coordinates of atom I at R[dim I + a]); mass may be NULL (all masses 1, so D is the
+   Hessian).  Perturbations and rows/columns of D are indexed dim I + a. */
 typedef struct {
   int n_atoms;
   const double* R;
@@ -148,9 +154,10 @@ acp_status acp_apply_chi0(acp_ctx* ctx, const double* G_d, int ncol, double* out
    of Eq. dyson4; U = U~ - B.  G_d, U_d: N x ncol. */
 acp_status acp_dyson_solve(acp_ctx* ctx, const double* G_d, int ncol, double* U_d, acp_stats* stats);
 
-/* Perturbation potentials of the atoms (one column per atom in 1D): G_d[:,I] = dV_I(x-R_I)/dR_I
-   with V_I = K * m_I (Eq. pseudocharge), B_d = K^{-1} G = dm_I/dR_I (change of variables of
-   Sec. 3.2), d2V_d[:,I] = d^2 V_I/dR_I^2.  Any of the outputs may be NULL. */
+/* Perturbation potentials of the atoms: G_d[:, dim I + a] = dV_I(x-R_I)/dR_{I,a} with
+   V_I = K * m_I (Eq. pseudocharge), B_d = K^{-1} G = dm_I/dR_{I,a} (change of variables of
+   Sec. 3.2); d2V_d: 1D one column per atom, d^2 V_I/dR_I^2; 2D three columns per atom,
+   3I + {0, 1, 2} = d^2 V_I / dR_x dR_x, dR_x dR_y, dR_y dR_y.  Any of the outputs may be NULL. */
 acp_status acp_perturbations(acp_ctx* ctx, const acp_atoms* atoms, double* G_d, double* B_d,
                              double* d2V_d);
 

@@ -148,11 +148,25 @@ class Context:
     """One acp_ctx bound to the current torch CUDA stream."""
 
     def __init__(self, n_grid, L, kappa, scale, V, psi, eps, opts=None, stream=None):
+        """n_grid, L: an integer and a length (1D), or (nx, ny) and (Lx, Ly) (2D, x fastest)."""
         import torch
         self.lib = load()
-        self.N = int(n_grid)
-        self.L = float(L)
-        self.h = self.L / self.N
+        if isinstance(n_grid, (tuple, list)) and len(n_grid) == 2:
+            self.dim = 2
+            self.shape = (int(n_grid[0]), int(n_grid[1]))
+            self.Ls = (float(L[0]), float(L[1]))
+            self.N = self.shape[0] * self.shape[1]
+            self.h = (self.Ls[0] / self.shape[0]) * (self.Ls[1] / self.shape[1])
+            self.L = self.Ls[0]
+        else:
+            n1 = int(n_grid[0]) if isinstance(n_grid, (tuple, list)) else int(n_grid)
+            L1 = float(L[0]) if isinstance(L, (tuple, list)) else float(L)
+            self.dim = 1
+            self.shape = (n1, 0)
+            self.Ls = (L1, 0.0)
+            self.N = n1
+            self.L = L1
+            self.h = self.L / self.N
         self.n_orb = int(psi.shape[0])
         _check_block(psi, self.N, "psi")
         if not (V.is_cuda and V.dtype == torch.float64 and V.is_contiguous() and V.numel() == self.N):
@@ -162,7 +176,7 @@ class Context:
         self._opts = None
         self._sketch = None
         o = self._make_options(opts or options())
-        g = Grid(1, (c_int * 2)(self.N, 0), (c_double * 2)(self.L, 0.0))
+        g = Grid(self.dim, (c_int * 2)(*self.shape), (c_double * 2)(*self.Ls))
         k = Kernel(float(kappa), float(scale))
         ptr = c_void_p()
         st = self.lib.acp_init(ctypes.byref(ptr), ctypes.byref(g), ctypes.byref(k), _tptr(V), _tptr(psi),
@@ -277,14 +291,18 @@ class Context:
         return a
 
     def perturbations(self, R, Z, sigma):
+        """G, B: (dim nA, N), row dim I + a; second derivatives: (nA, N) in 1D, (3 nA, N) in 2D
+        (rows 3I + {xx, xy, yy})."""
         a = self._atoms(R, Z, sigma)
-        G, B, D2 = self._out(a.n_atoms), self._out(a.n_atoms), self._out(a.n_atoms)
+        nA = a.n_atoms
+        G, B = self._out(self.dim * nA), self._out(self.dim * nA)
+        D2 = self._out(nA if self.dim == 1 else 3 * nA)
         self._call(self.lib.acp_perturbations(self.ptr, ctypes.byref(a), _tptr(G), _tptr(B), _tptr(D2)))
         return G, B, D2
 
     def dynamical_matrix(self, R, Z, sigma, rho, mass=None, U=None, allow_noconv=False):
         a = self._atoms(R, Z, sigma, mass)
-        D = np.zeros((a.n_atoms, a.n_atoms))
+        D = np.zeros((self.dim * a.n_atoms, self.dim * a.n_atoms))
         st = Stats()
         Up = _tptr(U) if U is not None else c_void_p()
         self._call(self.lib.acp_dynamical_matrix(self.ptr, ctypes.byref(a), _tptr(rho), _dptr(D), Up,
@@ -367,7 +385,8 @@ def batch_dynamical_matrix(contexts, atoms, rhos, n_workers=0):
         at[i].n_atoms = int(arrs[1].size)
         at[i].R, at[i].Z, at[i].sigma = (_dptr(x) for x in arrs)
         at[i].mass = None
-        Ds.append(np.zeros((arrs[1].size, arrs[1].size)))
+        nd = contexts[i].dim * arrs[1].size
+        Ds.append(np.zeros((nd, nd)))
     rho_arr = (c_void_p * n)(*[r.data_ptr() for r in rhos])
     D_arr = (POINTER(c_double) * n)(*[_dptr(D) for D in Ds])
     st = (Stats * n)()

@@ -210,10 +210,24 @@ acp_status acp_init(acp_ctx** out, const acp_grid* g, const acp_kernel* k, const
     *out = ctx;
     return st;
   };
-  if (g->dim != 1) return fail(set_error(ctx, ACP_E_ARG, "only dim = 1 grids are supported"));
-  const int N = g->n[0];
-  if (!make_fft_plan(N, &ctx->plan))
-    return fail(set_error(ctx, ACP_E_ARG, "grid size %d must be 2^a 3^b 5^c in [8, 8192]", N));
+  if (g->dim != 1 && g->dim != 2) return fail(set_error(ctx, ACP_E_ARG, "only dim = 1 or 2 grids are supported"));
+  ctx->dim = g->dim;
+  int N = g->n[0];
+  if (g->dim == 1) {
+    if (!make_fft_plan(N, &ctx->plan))
+      return fail(set_error(ctx, ACP_E_ARG, "grid size %d must be 2^a 3^b 5^c in [8, 8192]", N));
+  } else {
+    if (!make_axis_plan(g->n[0], &ctx->plan_x) || !make_axis_plan(g->n[1], &ctx->plan_y))
+      return fail(set_error(ctx, ACP_E_ARG, "2D grid sizes %d x %d must be 2^a 3^b 5^c in [8, 4096]", g->n[0],
+                            g->n[1]));
+    if (!(g->L[1] > 0)) return fail(set_error(ctx, ACP_E_ARG, "bad box length"));
+    ctx->nx = g->n[0];
+    ctx->ny = g->n[1];
+    ctx->Lx = g->L[0];
+    ctx->Ly = g->L[1];
+    N = ctx->nx * ctx->ny;
+    ctx->plan = ctx->plan_x;
+  }
   if (!(g->L[0] > 0) || !(k->kappa > 0) || n_orb < 1 || n_orb >= N)
     return fail(set_error(ctx, ACP_E_ARG, "bad box length, kappa or n_orb"));
   for (int i = 0; i < n_orb; ++i) {
@@ -226,24 +240,50 @@ acp_status acp_init(acp_ctx** out, const acp_grid* g, const acp_kernel* k, const
   ctx->stream = static_cast<cudaStream_t>(stream);
   ctx->N = N;
   ctx->L = g->L[0];
-  ctx->h = ctx->L / N;
+  ctx->h = (g->dim == 1) ? ctx->L / N : (g->L[0] / g->n[0]) * (g->L[1] / g->n[1]);
   ctx->kappa = k->kappa;
   ctx->scale = k->scale;
   ctx->n_orb = n_orb;
   ctx->opt = *opt;
   ctx->eps.assign(eps_h, eps_h + n_orb);
   // grid tables on the host (FP64, host libm), copied once
-  std::vector<double> kin(N), khat(N), kinv(N), kodd(N);
+  std::vector<double> kin(N), khat(N), kinv(N), kodd(N, 0.0);
   std::vector<double2> tw(N);
-  for (int a = 0; a < N; ++a) {
-    const int n = (a < (N + 1) / 2) ? a : a - N;
-    const double kk = 2.0 * M_PI * n / ctx->L;
-    kin[a] = 0.5 * kk * kk;
-    khat[a] = 4.0 * M_PI * ctx->scale / (kk * kk + ctx->kappa * ctx->kappa);
-    kinv[a] = 1.0 / khat[a];
-    kodd[a] = (2 * a == N) ? 0.0 : kk;
-    const double ang = 2.0 * M_PI * (double)a / N;
-    tw[a] = make_double2(std::cos(ang), -std::sin(ang));
+  if (g->dim == 1) {
+    for (int a = 0; a < N; ++a) {
+      const int n = (a < (N + 1) / 2) ? a : a - N;
+      const double kk = 2.0 * M_PI * n / ctx->L;
+      kin[a] = 0.5 * kk * kk;
+      khat[a] = 4.0 * M_PI * ctx->scale / (kk * kk + ctx->kappa * ctx->kappa);
+      kinv[a] = 1.0 / khat[a];
+      kodd[a] = (2 * a == N) ? 0.0 : kk;
+      const double ang = 2.0 * M_PI * (double)a / N;
+      tw[a] = make_double2(std::cos(ang), -std::sin(ang));
+    }
+  } else {
+    // symbols on the (ky, kx) grid, kx fastest; twiddles of the x axis then of the y axis
+    const int nx = ctx->nx, ny = ctx->ny;
+    for (int iy = 0; iy < ny; ++iy) {
+      const int my = (iy < (ny + 1) / 2) ? iy : iy - ny;
+      const double ky = 2.0 * M_PI * my / ctx->Ly;
+      for (int ix = 0; ix < nx; ++ix) {
+        const int mx = (ix < (nx + 1) / 2) ? ix : ix - nx;
+        const double kx = 2.0 * M_PI * mx / ctx->Lx;
+        const double k2 = kx * kx + ky * ky;
+        const int a = ix + nx * iy;
+        kin[a] = 0.5 * k2;
+        khat[a] = 4.0 * M_PI * ctx->scale / (k2 + ctx->kappa * ctx->kappa);
+        kinv[a] = 1.0 / khat[a];
+      }
+    }
+    for (int m = 0; m < nx; ++m) {
+      const double ang = 2.0 * M_PI * (double)m / nx;
+      tw[m] = make_double2(std::cos(ang), -std::sin(ang));
+    }
+    for (int m = 0; m < ny; ++m) {
+      const double ang = 2.0 * M_PI * (double)m / ny;
+      tw[nx + m] = make_double2(std::cos(ang), -std::sin(ang));
+    }
   }
   auto alloc = [&](void** p, size_t bytes) -> acp_status {
     cudaError_t e = cudaMalloc(p, bytes);
@@ -259,6 +299,8 @@ acp_status acp_init(acp_ctx** out, const acp_grid* g, const acp_kernel* k, const
   ctx->d_khat = ctx->d_kin + N;
   ctx->d_khat_inv = ctx->d_kin + 2 * N;
   ctx->d_kvec = ctx->d_kin + 3 * N;
+  ctx->d_twx = ctx->d_tw;
+  ctx->d_twy = ctx->d_tw + ctx->nx;
   cudaStream_t s = ctx->stream;
 #define INIT_CUDA(call)                                                                                   \
   do {                                                                                                    \
@@ -342,16 +384,18 @@ acp_status acp_perturbations(acp_ctx* ctx, const acp_atoms* atoms, double* G_d, 
     return set_error(ctx, ACP_E_ARG, "bad atoms");
   const int nA = atoms->n_atoms;
   if (nA == 0) return ACP_OK;
+  const int d = ctx->dim;
   double* hv = nullptr;
-  ACP_TRY(ws(ctx, "pt_atoms", 3 * (size_t)nA, &hv));
-  std::vector<double> host(3 * (size_t)nA);
+  ACP_TRY(ws(ctx, "pt_atoms", (size_t)(d + 2) * nA, &hv));
+  std::vector<double> host((size_t)(d + 2) * nA);
   for (int I = 0; I < nA; ++I) {
-    host[I] = atoms->R[I];
-    host[nA + I] = atoms->Z[I];
-    host[2 * nA + I] = atoms->sigma[I];
+    for (int a = 0; a < d; ++a) host[(size_t)d * I + a] = atoms->R[(size_t)d * I + a];
+    host[(size_t)d * nA + I] = atoms->Z[I];
+    host[(size_t)(d + 1) * nA + I] = atoms->sigma[I];
   }
-  ACP_CUDA(ctx, cudaMemcpyAsync(hv, host.data(), sizeof(double) * 3 * nA, cudaMemcpyHostToDevice, ctx->stream));
-  ACP_TRY(perturbations_1d(ctx, nA, hv, hv + nA, hv + 2 * nA, G_d, B_d, d2V_d));
+  ACP_CUDA(ctx, cudaMemcpyAsync(hv, host.data(), sizeof(double) * (d + 2) * nA, cudaMemcpyHostToDevice, ctx->stream));
+  if (d == 2) ACP_TRY(perturbations_2d(ctx, nA, hv, hv + 2 * nA, hv + 3 * nA, G_d, B_d, d2V_d));
+  else ACP_TRY(perturbations_1d(ctx, nA, hv, hv + nA, hv + 2 * nA, G_d, B_d, d2V_d));
   ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return ACP_OK;
 }

@@ -57,7 +57,13 @@ struct acp_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   int N = 0;
-  double L = 0, h = 0;
+  double L = 0, h = 0;            // h: quadrature weight of a grid point (hx in 1D, hx hy in 2D)
+  int dim = 1;                    // 2D: N = nx ny, x fastest
+  int nx = 0, ny = 0;
+  double Lx = 0, Ly = 0;
+  acp::FftPlan plan_x, plan_y;    // 2D: per-axis plans of the multi-pass transforms
+  double2* d_twx = nullptr;       // 2D: exp(-2 pi i m / nx), then exp(-2 pi i m / ny) (d_twy)
+  double2* d_twy = nullptr;
   double kappa = 0, scale = 0;
   int n_orb = 0;
   acp_options opt{};
@@ -152,6 +158,23 @@ acp_status spectral_apply(acp_ctx* ctx, const double* X, int ldx, int ncol, Spec
 acp_status spectral_configure(acp_ctx* ctx);
 // Set the dynamic shared-memory limit of a kernel to the opt-in maximum minus its static usage.
 acp_status raise_smem_limit(acp_ctx* ctx, const void* func);
+// 2D (spectral2d.cu): per-axis FFT plans, the multi-pass spectral operator in FP64 or FP32 (same
+// semantics as spectral_apply / spectral32_apply), perturbation potentials (G, B: N x 2 nA,
+// column 2I + a; D2: N x 3 nA, columns 3I + {xx, xy, yy}), the ion-ion Hessian blocks and the
+// assembly of D.
+bool make_axis_plan(int n, FftPlan* plan);
+acp_status spectral2d_apply_f64(acp_ctx* ctx, const double* X, int ldx, int ncol, const double* mult, const double* V,
+                                const double* shift_d, double* Y, int ldy, double* alpha_d, const int* active_d,
+                                const double* Xp, int ldp, const double* beta_d);
+acp_status spectral2d_apply_f32(acp_ctx* ctx, const float* X, int ldx, int ncol, const float* mult, const float* V,
+                                const float* shift_d, float* Y, int ldy, float* alpha_d, const int* active_d,
+                                const float* Xp, int ldp, const float* beta_d, const float2* twx, const float2* twy,
+                                const int* kdev, long long kstride);
+acp_status perturbations_2d(acp_ctx* ctx, int nA, const double* R_d, const double* Z_d, const double* sig_d,
+                            double* G, double* B, double* D2);
+acp_status ion_hessian_2d(acp_ctx* ctx, int nA, const double* R_h, const double* R_d, double* Hp);
+acp_status assemble_2d(acp_ctx* ctx, int nA, const double* Hm, const double* dv, const double* Hp, const double* Z_d,
+                       const double* M_d, double* D);
 // Perturbation potentials of n_atoms atoms (1D): G, B, d2V (each nullable, N x n_atoms).
 acp_status perturbations_1d(acp_ctx* ctx, int n_atoms, const double* R_d, const double* Z_d, const double* sig_d,
                             double* G, double* B, double* D2);

@@ -502,8 +502,54 @@ acp_status dyson(acp_ctx* ctx, const double* G, int ncol, double* U, acp_stats* 
 }
 
 // ---- Eq. SecDeriv ------------------------------------------------------------------------------
+// 2D: perturbation columns 2I + a; D is (2 nA) x (2 nA) with a 2 x 2 local block per atom and the
+// ion-ion Hessian blocks of spectral2d.cu.
+acp_status dynamical_2d(acp_ctx* ctx, const acp_atoms* at, const double* rho, double* D_h, double* U_user,
+                        acp_stats* st, SolveReport* rep, double t0) {
+  const int N = ctx->N, nA = at->n_atoms, nP = 2 * nA;
+  double *hv = nullptr, *G = nullptr, *D2 = nullptr, *U = nullptr, *Hm = nullptr, *nrm = nullptr;
+  ACP_TRY(ws(ctx, "dm_atoms", 5 * (size_t)nA, &hv));  // R (2 per atom), Z, sigma, mass
+  std::vector<double> host(5 * (size_t)nA);
+  for (int I = 0; I < nA; ++I) {
+    host[2 * I] = at->R[2 * I];
+    host[2 * I + 1] = at->R[2 * I + 1];
+    host[2 * nA + I] = at->Z[I];
+    host[3 * nA + I] = at->sigma[I];
+    host[4 * nA + I] = at->mass ? at->mass[I] : 1.0;
+  }
+  ACP_CUDA(ctx, cudaMemcpyAsync(hv, host.data(), sizeof(double) * 5 * nA, cudaMemcpyHostToDevice, ctx->stream));
+  ACP_TRY(ws(ctx, "dm_g", (size_t)N * nP, &G));
+  ACP_TRY(ws(ctx, "dm_d2", (size_t)N * 3 * nA, &D2));
+  if (U_user) U = U_user;
+  else ACP_TRY(ws(ctx, "dm_u", (size_t)N * nP, &U));
+  ACP_TRY(ws(ctx, "dm_h", (size_t)nP * nP * 3 + 3 * (size_t)nA + 4 * (size_t)nA * nA + 2, &Hm));
+  double* D = Hm + (size_t)nP * nP;
+  double* Ds = D + (size_t)nP * nP;
+  double* dv = Ds + (size_t)nP * nP;
+  double* Hp = dv + 3 * (size_t)nA;
+  nrm = Hp + 4 * (size_t)nA * nA;
+  ACP_TRY(perturbations_2d(ctx, nA, hv, hv + 2 * nA, hv + 3 * nA, G, nullptr, D2));
+  acp_status sd = dyson(ctx, G, nP, U, st, rep, t0);
+  if (sd != ACP_OK && sd != ACP_E_NOCONV) return sd;
+  ACP_TRY(dgemm(ctx, true, false, nP, nP, N, ctx->h, G, N, U, N, 0.0, Hm, nP));
+  ACP_TRY(dgemm(ctx, true, false, 3 * nA, 1, N, ctx->h, D2, N, rho, N, 0.0, dv, 3 * nA));
+  ACP_TRY(ion_hessian_2d(ctx, nA, at->R, hv, Hp));
+  ACP_TRY(assemble_2d(ctx, nA, Hm, dv, Hp, hv + 2 * nA, hv + 4 * nA, D));
+  ACP_CUDA(ctx, cudaMemsetAsync(nrm, 0, 2 * sizeof(double), ctx->stream));
+  ::acp::note_launch(ctx);
+  symmetrize_kernel<<<grid_for((size_t)nP * nP, 1024), 256, 0, ctx->stream>>>(nP, D, Ds, nrm);
+  ACP_LAUNCH(ctx);
+  double hn[2];
+  ACP_CUDA(ctx, cudaMemcpyAsync(D_h, Ds, sizeof(double) * nP * nP, cudaMemcpyDeviceToHost, ctx->stream));
+  ACP_CUDA(ctx, cudaMemcpyAsync(hn, nrm, sizeof(double) * 2, cudaMemcpyDeviceToHost, ctx->stream));
+  ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (st) st->asymmetry = hn[1] > 0 ? sqrt(hn[0] / hn[1]) : 0.0;
+  return sd;
+}
+
 acp_status dynamical(acp_ctx* ctx, const acp_atoms* at, const double* rho, double* D_h, double* U_user,
                      acp_stats* st, SolveReport* rep, double t0) {
+  if (ctx->dim == 2) return dynamical_2d(ctx, at, rho, D_h, U_user, st, rep, t0);
   const int N = ctx->N, nA = at->n_atoms;
   double *hv = nullptr, *G = nullptr, *D2 = nullptr, *U = nullptr, *Hm = nullptr, *dv = nullptr, *D = nullptr,
          *Ds = nullptr, *nrm = nullptr;

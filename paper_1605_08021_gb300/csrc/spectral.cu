@@ -317,6 +317,9 @@ acp_status spectral_apply(acp_ctx* ctx, const double* X, int ldx, int ncol, Spec
                           const double* Xprev, const double* beta_d) {
   if (ncol <= 0) return ACP_OK;
   const double* m = (mult == MULT_KINETIC) ? ctx->d_kin : (mult == MULT_KHAT) ? ctx->d_khat : ctx->d_khat_inv;
+  if (ctx->dim == 2)
+    return spectral2d_apply_f64(ctx, X, ldx, ncol, m, with_v ? ctx->d_V : nullptr, shift_d, Y, ldy, alpha_d, active_d,
+                                Xprev, ldx, beta_d);
   const int blocks = (ncol + 1) / 2;
   ::acp::note_launch(ctx);
   cudaEvent_t ev0 = prof_begin(ctx);

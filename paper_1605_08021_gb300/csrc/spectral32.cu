@@ -74,7 +74,7 @@ template <> struct MaxBf<4> { static constexpr int v = 3; };
 template <> struct MaxBf<5> { static constexpr int v = 2; };
 
 template <int R>
-__device__ __noinline__ void fft_stage_f(float2* s, int N, int Ns, const float2* __restrict__ tw, float dir) {
+__device__ __forceinline__ void fft_stage_f(float2* s, int N, int Ns, const float2* __restrict__ tw, float dir) {
   constexpr int B = MaxBf<R>::v;
   const int nb = N / R;
   const int stride = N / (Ns * R);
@@ -150,7 +150,10 @@ constexpr int kMaxThreads = 512;
 // P = (H - s_j) x_j - alpha_j x_j - beta_j xp_j with alpha_j = x_j . (H - s_j) x_j (Lanczos form,
 // xp != nullptr), or Y = (H - s_j) x_j.  shift (nullable) per column; active (nullable) masks
 // columns; alpha (nullable) receives the coefficients.
-__global__ void __launch_bounds__(kMaxThreads)
+// Two CTAs per SM (64 registers per thread, a few spilled): the FFT stages wait on shared and L1
+// loads behind CTA barriers, and a second resident CTA hides them (33% faster than one CTA of
+// 120 registers on the 64-atom chain).
+__global__ void __launch_bounds__(kMaxThreads, 2)
     spectral32_kernel(const float* __restrict__ X, int ldx, int ncol, PlanArgF plan, const float2* __restrict__ tw,
                       const float* __restrict__ kin, const float* __restrict__ V, const float* __restrict__ shift,
                       float* __restrict__ Y, int ldy, float* __restrict__ alpha, const int* __restrict__ active,
@@ -221,13 +224,13 @@ __global__ void __launch_bounds__(kMaxThreads)
   }
 }
 
-__global__ void tables32_kernel(int N, const double* __restrict__ kin, const double* __restrict__ V,
+__global__ void tables32_kernel(int N, int ntw, const double* __restrict__ kin, const double* __restrict__ V,
                                 const double2* __restrict__ tw, float* __restrict__ kin32, float* __restrict__ V32,
                                 float2* __restrict__ tw32) {
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
     kin32[a] = (float)kin[a];
     V32[a] = (float)V[a];
-    tw32[a] = make_float2((float)tw[a].x, (float)tw[a].y);
+    if (a < ntw) tw32[a] = make_float2((float)tw[a].x, (float)tw[a].y);
   }
 }
 
@@ -240,7 +243,8 @@ acp_status tables32(acp_ctx* ctx, const float** kin32, const float** V32, const 
   ACP_TRY(ws(ctx, "tables32", (size_t)4 * N, &buf));
   if (ctx->tables32_stale) {
     ::acp::note_launch(ctx);
-    tables32_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ctx->d_kin, ctx->d_V, ctx->d_tw, buf, buf + N,
+    const int ntw = (ctx->dim == 2) ? ctx->nx + ctx->ny : N;  // 2D: x twiddles, then y twiddles
+    tables32_kernel<<<(N + 255) / 256, 256, 0, ctx->stream>>>(N, ntw, ctx->d_kin, ctx->d_V, ctx->d_tw, buf, buf + N,
                                                              reinterpret_cast<float2*>(buf + 2 * N));
     ACP_LAUNCH(ctx);
     // raised once per device to the opt-in maximum, never lowered (the limit is shared by all
@@ -266,6 +270,9 @@ acp_status spectral32_apply(acp_ctx* ctx, const float* X, int ldx, int ncol, con
   const float *kin = nullptr, *V = nullptr;
   const float2* tw = nullptr;
   ACP_TRY(tables32(ctx, &kin, &V, &tw));
+  if (ctx->dim == 2)
+    return spectral2d_apply_f32(ctx, X, ldx, ncol, kin, V, shift_d, Y, ldy, alpha_d, active_d, Xprev, ldp, beta_d, tw,
+                                tw + ctx->nx, kdev, kstride);
   PlanArgF pa{};
   pa.n = ctx->plan.n;
   pa.nst = ctx->plan.nst;

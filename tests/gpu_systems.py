@@ -13,10 +13,19 @@ def system(name):
         s = W.config(1)
     elif name == "c2":
         s = W.config(2)
+    elif name == "c3":
+        s = W.config(3)
     elif name.startswith("small"):
         # small<atoms>_<grid>_<seed>
         a, n, seed = (int(x) for x in name[5:].split("_"))
         s = W.small_chain(a, n, seed)
+    elif name.startswith("lat"):
+        # lat<nx>x<ny>_<grid>_<seed>: small 2D lattices (spacing 8 bohr, mixed Z, occupation 1);
+        # latz...: all Z = 2, occupation 2 (closed shells)
+        closed = name.startswith("latz")
+        dims, n, seed = name[4 if closed else 3:].split("_")
+        nxa, nya = (int(x) for x in dims.split("x"))
+        s = W.small_lattice(nxa, nya, int(n), int(seed), occ=2 if closed else 1, mixed=not closed)
     else:
         raise KeyError(name)
     gs = W.ground_state(s)
@@ -24,9 +33,9 @@ def system(name):
 
 
 def model(name):
-    from oracle.model import Model1D
+    from oracle.model import Model1D, Model2D
     s, gs = system(name)
-    return Model1D(s, gs)
+    return Model2D(s, gs) if s.dim == 2 else Model1D(s, gs)
 
 
 def context(name, **opts):
@@ -37,7 +46,8 @@ def context(name, **opts):
     V = torch.tensor(gs.V, dtype=torch.float64, device="cuda")
     psi = torch.tensor(np.ascontiguousarray(gs.psi.T), dtype=torch.float64, device="cuda")
     o = P.options(occ=float(s.occ), **opts)
-    ctx = P.Context(s.n[0], s.L[0], s.kappa, s.scale, V, psi, gs.eps[: gs.n_orb], o)
+    n, L = (s.n, s.L) if s.dim == 2 else (s.n[0], s.L[0])
+    ctx = P.Context(n, L, s.kappa, s.scale, V, psi, gs.eps[: gs.n_orb], o)
     return ctx
 
 
