@@ -105,14 +105,19 @@ typedef struct {
                           eigenvectors, so Q only removes rounding-level occupied components; but
                           the shifts lie inside the occupied band, and occupied components left in
                           the basis for several steps can stall the residual (see minres.cu).    */
-  int ms_variant;      /* multi-shift MINRES storage: 0 automatic (stored Lanczos basis of up to 512
-                          steps when it fits in min(32 GB, half the free memory), else per-shift
-                          vectors), 1 stored basis, 2 per-shift vectors.  A stored-basis solve that
-                          needs more steps than its basis holds returns ACP_E_NOCONV.              */
+  int ms_variant;      /* FP64 multi-shift MINRES storage: 0 automatic (stored Lanczos basis of up to
+                          512 steps when at least 384 fit in min(32 GB, half the free memory), else
+                          per-shift vectors), 1 stored basis, 2 per-shift vectors.  A stored-basis
+                          solve that needs more steps than its basis holds returns ACP_E_NOCONV.
+                          (The FP32 pass of the mixed form always stores its basis, within
+                          min(16 GB, half the free memory); refinement completes it.)              */
   int precision;       /* ACP_PREC_FP64 or ACP_PREC_MIXED (see above)                            */
   int use_graphs;      /* mixed precision: capture 16-step chunks of the FP32 Lanczos loops once as
                           CUDA graphs and replay them (1), or launch every kernel (0).  Kernels
                           replayed from graphs are not timed by acp_profile_*.                      */
+  int fft2d_passes;    /* 2D grids: 0 transforms a column pair inside one CTA's shared memory when
+                          it fits, else in row / column passes through device memory; 1 always
+                          uses the passes.                                                          */
 } acp_options;
 
 typedef struct {
@@ -177,9 +182,10 @@ acp_status acp_dynamical_matrix(acp_ctx* ctx, const acp_atoms* atoms, const doub
    different systems overlap on their streams, and with use_graphs set in the contexts' options
    every 16-step chunk of the FP32 Lanczos loops is one CUDA graph launch.  atoms[i], rho_d[i],
    D_h[i] and stats[i] (nullable) are system i's arguments of acp_dynamical_matrix;
-   status_out (nullable, n_sys entries) receives each system's status.  Each context's device
-   workspace is released when its system is done (so the batch holds memory only for the
-   systems in flight; it regrows on the context's next call).  Returns ACP_OK, or the first
+   status_out (nullable, n_sys entries) receives each system's status.  Each worker carries one
+   set of device workspace buffers from system to system (the contexts' own buffers join it and
+   every context leaves the batch without workspace), so the batch holds memory only for the
+   systems in flight and allocates only when a larger system needs more.  Returns ACP_OK, or the first
    failing system's status (the others still run).  No counterpart in the paper, which treats
    one system at a time. */
 acp_status acp_batch_dynamical_matrix(acp_ctx* const* ctxs, int n_sys, const acp_atoms* atoms,

@@ -53,7 +53,7 @@ class Options(ctypes.Structure):
                 ("stern_tol", c_double), ("stern_maxit", c_int), ("dyson_tol", c_double),
                 ("dyson_maxit", c_int), ("rhs_batch", c_int), ("deadline_s", c_double),
                 ("project_every", c_int), ("ms_variant", c_int), ("precision", c_int),
-                ("use_graphs", c_int)]
+                ("use_graphs", c_int), ("fft2d_passes", c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -136,12 +136,13 @@ def _check_block(t, N, name):
 
 def options(method=ACP_METHOD_ACP, occ=1.0, n_cheb=16, id_tol=1e-5, sketch=None, max_rank=0,
             stern_tol=1e-11, stern_maxit=5000, dyson_tol=1e-10, dyson_maxit=30, rhs_batch=0,
-            deadline_s=0.0, project_every=0, ms_variant=0, precision=0, use_graphs=0):
+            deadline_s=0.0, project_every=0, ms_variant=0, precision=0, use_graphs=0, fft2d_passes=0):
     """Options as a dict (the sketch Omega, if given, is an (n_cols, r) float64 array)."""
     return dict(method=method, occ=occ, n_cheb=n_cheb, id_tol=id_tol, sketch=sketch, max_rank=max_rank,
                 stern_tol=stern_tol, stern_maxit=stern_maxit, dyson_tol=dyson_tol, dyson_maxit=dyson_maxit,
                 rhs_batch=rhs_batch, deadline_s=deadline_s, project_every=project_every,
-                ms_variant=ms_variant, precision=precision, use_graphs=use_graphs)
+                ms_variant=ms_variant, precision=precision, use_graphs=use_graphs,
+                fft2d_passes=fft2d_passes)
 
 
 class Context:
@@ -215,6 +216,7 @@ class Context:
         o.ms_variant = int(d.get("ms_variant", 0))
         o.precision = int(d.get("precision", 0))
         o.use_graphs = int(d.get("use_graphs", 0))
+        o.fft2d_passes = int(d.get("fft2d_passes", 0))
         self._opts = o
         return o
 

@@ -320,6 +320,12 @@ acp_status acp_init(acp_ctx** out, const acp_grid* g, const acp_kernel* k, const
 #undef INIT_CUDA
   st = spectral_configure(ctx);
   if (st != ACP_OK) return fail(st);
+  {
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device) == cudaSuccess)
+      ctx->smem_optin = (size_t)optin;
+    cudaGetLastError();
+  }
   *out = ctx;
   return ACP_OK;
 }
@@ -432,27 +438,54 @@ acp_status acp_batch_dynamical_matrix(acp_ctx* const* ctxs, int n_sys, const acp
   std::vector<int> order(n_sys);
   for (int i = 0; i < n_sys; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctxs[a]->N > ctxs[b]->N; });
-  auto worker = [&]() {
+  // Each worker carries one set of workspace buffers from system to system (moved into the
+  // context before its run and back out after), so the batch holds memory for the systems in
+  // flight only and allocates (cudaMalloc / cudaFree synchronise the device) only when a larger
+  // system needs more; what the workers hold at the end is freed.
+  std::vector<std::map<std::string, std::pair<void*, size_t>>> held(workers);
+  auto worker = [&](int w) {
     for (;;) {
       const int q = next.fetch_add(1);
       if (q >= n_sys) return;
       const int i = order[q];
-      st[i] = acp_dynamical_matrix(ctxs[i], &atoms[i], rho_d[i], D_h[i], nullptr, stats ? &stats[i] : nullptr);
-      // hand the system's workspace back, so that the device memory of the batch is bounded by
-      // the systems in flight rather than by all of them (it regrows on the context's next call)
-      cudaStreamSynchronize(ctxs[i]->stream);
-      std::lock_guard<std::mutex> lock(device_mutex());
-      for (auto& kv : ctxs[i]->ws.bufs)
-        if (kv.second.first) cudaFree(kv.second.first);
-      ctxs[i]->ws.bufs.clear();
-      ctxs[i]->psi32_stale = true;
-      ctxs[i]->tables32_stale = true;
+      acp_ctx* c = ctxs[i];
+      cudaSetDevice(c->device);
+      cudaStreamSynchronize(c->stream);
+      for (auto& kv : c->ws.bufs) {  // the context's own buffers join the worker's set
+        auto it = held[w].find(kv.first);
+        if (it == held[w].end() || it->second.second < kv.second.second) {
+          if (it != held[w].end()) {
+            std::lock_guard<std::mutex> lock(device_mutex());
+            cudaFree(it->second.first);
+          }
+          held[w][kv.first] = kv.second;
+        } else {
+          std::lock_guard<std::mutex> lock(device_mutex());
+          cudaFree(kv.second.first);
+        }
+      }
+      c->ws.bufs = std::move(held[w]);
+      held[w].clear();
+      c->psi32_stale = true;  // the buffers hold another system's data
+      c->tables32_stale = true;
+      st[i] = acp_dynamical_matrix(c, &atoms[i], rho_d[i], D_h[i], nullptr, stats ? &stats[i] : nullptr);
+      cudaStreamSynchronize(c->stream);
+      held[w] = std::move(c->ws.bufs);
+      c->ws.bufs.clear();
+      c->psi32_stale = true;
+      c->tables32_stale = true;
     }
   };
   std::vector<std::thread> pool;
-  for (int w = 1; w < workers; ++w) pool.emplace_back(worker);
-  worker();
+  for (int w = 1; w < workers; ++w) pool.emplace_back(worker, w);
+  worker(0);
   for (auto& t : pool) t.join();
+  {
+    std::lock_guard<std::mutex> lock(device_mutex());
+    for (auto& h : held)
+      for (auto& kv : h)
+        if (kv.second.first) cudaFree(kv.second.first);
+  }
   acp_status worst = ACP_OK;
   for (int i = 0; i < n_sys; ++i) {
     if (status_out) status_out[i] = st[i];

@@ -64,6 +64,7 @@ struct acp_ctx {
   acp::FftPlan plan_x, plan_y;    // 2D: per-axis plans of the multi-pass transforms
   double2* d_twx = nullptr;       // 2D: exp(-2 pi i m / nx), then exp(-2 pi i m / ny) (d_twy)
   double2* d_twy = nullptr;
+  size_t smem_optin = 0;          // dynamic shared memory a CTA may use on this device
   double kappa = 0, scale = 0;
   int n_orb = 0;
   acp_options opt{};

@@ -693,7 +693,9 @@ acp_status minres_multishift(acp_ctx* ctx, const double* B, int nmu, const doubl
     int kmax = ctx->opt.stern_maxit;
     if (kmax > 512) kmax = 512;
     if ((size_t)kmax + 2 > fit) kmax = (int)fit - 2;
-    if (kmax >= 64 || ctx->opt.ms_variant == 1)
+    // the basis must hold a whole solve: with fewer than 384 slots (large grids with many
+    // points) the per-shift-vector variant is used instead
+    if (kmax >= 384 || ctx->opt.ms_variant == 1)
       return minres_multishift_basis(ctx, B, nmu, nodes_d, nc, X, kmax < 1 ? 1 : kmax, rep, t0_ms);
   }
   return minres_multishift_vectors(ctx, B, nmu, nodes_d, nc, X, rep, t0_ms);

@@ -102,9 +102,11 @@ struct AxisPlan {
 // One in-place Stockham stage of every transform of the CTA: thread `tid` of a group of `nt`
 // threads works on the length-n signal at s.  All groups call it together (CTA barriers);
 // groups without a signal pass valid = false.
+// wsync: the group is one whole warp working on its own signal, so the stage synchronises the warp
+// only (no CTA barrier; warps then run their transforms independently).
 template <int R, class T2, class T>
 __device__ __noinline__ void stage2(T2* s, int n, int Ns, const T2* __restrict__ tw, T dir, int tid, int nt,
-                                    bool valid) {
+                                    bool valid, int es, bool wsync) {
   constexpr int B = Mb<R>::v;
   const int nb = n / R;
   const int stride = n / (Ns * R);
@@ -115,11 +117,12 @@ __device__ __noinline__ void stage2(T2* s, int n, int Ns, const T2* __restrict__
       const int j = tid + b * nt;
       if (j < nb) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) a[b][r] = s[j + r * nb];
+        for (int r = 0; r < R; ++r) a[b][r] = s[(j + r * nb) * es];
       }
     }
   }
-  __syncthreads();
+  if (wsync) __syncwarp();
+  else __syncthreads();
   if (valid) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
@@ -135,22 +138,25 @@ __device__ __noinline__ void stage2(T2* s, int n, int Ns, const T2* __restrict__
         Dft<R, T2, T>::run(a[b], dir);
         const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[base + r * Ns] = a[b][r];
+        for (int r = 0; r < R; ++r) s[(base + r * Ns) * es] = a[b][r];
       }
     }
   }
-  __syncthreads();
+  if (wsync) __syncwarp();
+  else __syncthreads();
 }
 
+// Transform of a length-n signal whose element i sits at s[i * es] (es = 1: contiguous).
 template <class T2, class T>
-__device__ void fft_grp(T2* s, const AxisPlan& p, const T2* __restrict__ tw, T dir, int tid, bool valid) {
+__device__ void fft_grp(T2* s, const AxisPlan& p, const T2* __restrict__ tw, T dir, int tid, bool valid, int es = 1,
+                        bool wsync = false) {
   int Ns = 1;
   for (int st = 0; st < p.nst; ++st) {
     switch (p.rad[st]) {
-      case 4: stage2<4, T2, T>(s, p.n, Ns, tw, dir, tid, p.nt, valid); break;
-      case 2: stage2<2, T2, T>(s, p.n, Ns, tw, dir, tid, p.nt, valid); break;
-      case 3: stage2<3, T2, T>(s, p.n, Ns, tw, dir, tid, p.nt, valid); break;
-      default: stage2<5, T2, T>(s, p.n, Ns, tw, dir, tid, p.nt, valid); break;
+      case 4: stage2<4, T2, T>(s, p.n, Ns, tw, dir, tid, p.nt, valid, es, wsync); break;
+      case 2: stage2<2, T2, T>(s, p.n, Ns, tw, dir, tid, p.nt, valid, es, wsync); break;
+      case 3: stage2<3, T2, T>(s, p.n, Ns, tw, dir, tid, p.nt, valid, es, wsync); break;
+      default: stage2<5, T2, T>(s, p.n, Ns, tw, dir, tid, p.nt, valid, es, wsync); break;
     }
     Ns *= p.rad[st];
   }
@@ -330,6 +336,115 @@ __global__ void __launch_bounds__(512) rows_inv_kernel(PassArgs a, int mode, con
     if (threadIdx.x == 0) {
       if (act0) atomicAdd(&alpha[c0], dot0);
       if (act1) atomicAdd(&alpha[c1], dot1);
+    }
+  }
+}
+
+// Whole 2D transform of one column pair in shared memory (one CTA per pair; the ny x nx signal is
+// stored with a row stride of nx + 1 to spread column accesses over the banks): row FFTs, column
+// FFTs, symbol, inverse column and row FFTs, then y = z / N + (V - s) x, alpha = x . y within the
+// CTA, and in the Lanczos form P = y - alpha x - beta x_prev -- the 1D kernel's structure, for
+// grids whose signal fits in shared memory.
+template <class T>
+__global__ void __launch_bounds__(512) fused2d_kernel(PassArgs a, const T* __restrict__ X, int ldx,
+                                                      const typename Cx<T>::t* __restrict__ twx,
+                                                      const typename Cx<T>::t* __restrict__ twy,
+                                                      const T* __restrict__ mult, const T* __restrict__ V,
+                                                      const T* __restrict__ shift, T* __restrict__ Y, int ldy,
+                                                      T* __restrict__ alpha, const T* __restrict__ Xp, int ldp,
+                                                      const T* __restrict__ beta) {
+  using T2 = typename Cx<T>::t;
+  extern __shared__ __align__(16) unsigned char smem2d[];
+  __shared__ T red[32];
+  T2* s = reinterpret_cast<T2*>(smem2d);
+  const int p = blockIdx.x, c0 = 2 * p, c1 = c0 + 1;
+  const bool act0 = !a.active || a.active[c0];
+  const bool act1 = c1 < a.ncol && (!a.active || a.active[c1]);
+  if (!act0 && !act1) return;
+  const int nx = a.nx, ny = a.ny, ld = nx + 1;
+  const int N = nx * ny;
+  const T* x0 = colptr(X, ldx, c0, a.kdev, a.kstride, 0);
+  const T* x1 = colptr(X, ldx, c1, a.kdev, a.kstride, 0);
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const int ix = e % nx, iy = e / nx;
+    s[iy * ld + ix] = mk<T2>(act0 ? x0[e] : T(0), act1 ? x1[e] : T(0));
+  }
+  __syncthreads();
+  if (a.px.nt == 32 && a.py.nt == 32) {
+    // one warp per row / column, each warp through its own signals without CTA barriers
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int iy = warp; iy < ny; iy += nw) fft_grp<T2, T>(s + (size_t)iy * ld, a.px, twx, T(-1), lane, true, 1, true);
+    __syncthreads();
+    for (int kx = warp; kx < nx; kx += nw) {
+      T2* col = s + kx;
+      fft_grp<T2, T>(col, a.py, twy, T(-1), lane, true, ld, true);
+      for (int iy = lane; iy < ny; iy += 32) col[iy * ld] = cscale2<T2, T>(col[iy * ld], mult[iy * nx + kx]);
+      __syncwarp();
+      fft_grp<T2, T>(col, a.py, twy, T(1), lane, true, ld, true);
+    }
+    __syncthreads();
+    for (int iy = warp; iy < ny; iy += nw) fft_grp<T2, T>(s + (size_t)iy * ld, a.px, twx, T(1), lane, true, 1, true);
+    __syncthreads();
+  } else {
+    const int gx = blockDim.x / a.px.nt, gy = blockDim.x / a.py.nt;
+    const int rx = threadIdx.x / a.px.nt, tx = threadIdx.x % a.px.nt;
+    const int ry = threadIdx.x / a.py.nt, ty = threadIdx.x % a.py.nt;
+    for (int r0 = 0; r0 < ny; r0 += gx) {
+      const int iy = r0 + rx;
+      fft_grp<T2, T>(s + (size_t)(iy < ny ? iy : 0) * ld, a.px, twx, T(-1), tx, rx < gx && iy < ny);
+    }
+    for (int q0 = 0; q0 < nx; q0 += gy) {
+      const int kx = q0 + ry;
+      const bool valid = ry < gy && kx < nx;
+      T2* col = s + (valid ? kx : 0);
+      fft_grp<T2, T>(col, a.py, twy, T(-1), ty, valid, ld);
+      if (valid)
+        for (int iy = ty; iy < ny; iy += a.py.nt) col[iy * ld] = cscale2<T2, T>(col[iy * ld], mult[iy * nx + kx]);
+      __syncthreads();
+      fft_grp<T2, T>(col, a.py, twy, T(1), ty, valid, ld);
+    }
+    for (int r0 = 0; r0 < ny; r0 += gx) {
+      const int iy = r0 + rx;
+      fft_grp<T2, T>(s + (size_t)(iy < ny ? iy : 0) * ld, a.px, twx, T(1), tx, rx < gx && iy < ny);
+    }
+  }
+  const T invN = T(1) / T(N);
+  const T sh0 = (shift && act0) ? shift[c0] : T(0);
+  const T sh1 = (shift && act1) ? shift[c1] : T(0);
+  T dot0 = 0, dot1 = 0;
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const int ix = e % nx, iy = e / nx;
+    const T v = V ? V[e] : T(0);
+    const T xa0 = act0 ? x0[e] : T(0), xa1 = act1 ? x1[e] : T(0);
+    const T2 z = s[iy * ld + ix];
+    const T y0 = z.x * invN + (v - sh0) * xa0;
+    const T y1 = z.y * invN + (v - sh1) * xa1;
+    dot0 += xa0 * y0;
+    dot1 += xa1 * y1;
+    s[iy * ld + ix] = mk<T2>(y0, y1);
+  }
+  const bool lanczos = Xp != nullptr;
+  if (alpha || lanczos) {
+    dot0 = block_sum_t(dot0, red);
+    dot1 = block_sum_t(dot1, red);
+    if (alpha && threadIdx.x == 0) {
+      if (act0) alpha[c0] = dot0;
+      if (act1) alpha[c1] = dot1;
+    }
+  }
+  __syncthreads();
+  const T b0 = (lanczos && act0) ? beta[c0] : T(0), b1 = (lanczos && act1) ? beta[c1] : T(0);
+  const T* p0 = lanczos ? colptr(Xp, ldp, c0, a.kdev, a.kstride, -1) : nullptr;
+  const T* p1 = lanczos ? colptr(Xp, ldp, c1, a.kdev, a.kstride, -1) : nullptr;
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const int ix = e % nx, iy = e / nx;
+    const T2 yv = s[iy * ld + ix];
+    if (lanczos) {
+      if (act0) Y[(size_t)c0 * ldy + e] = yv.x - dot0 * x0[e] - b0 * p0[e];
+      if (act1) Y[(size_t)c1 * ldy + e] = yv.y - dot1 * x1[e] - b1 * p1[e];
+    } else {
+      if (act0) Y[(size_t)c0 * ldy + e] = yv.x;
+      if (act1) Y[(size_t)c1 * ldy + e] = yv.y;
     }
   }
 }
@@ -528,6 +643,8 @@ acp_status spectral2d_apply(acp_ctx* ctx, const T* X, int ldx, int ncol, const T
       ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(cols_kernel<float>)));
       ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(rows_inv_kernel<double>)));
       ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(rows_inv_kernel<float>)));
+      ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(fused2d_kernel<double>)));
+      ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(fused2d_kernel<float>)));
       configured_device = ctx->device;
     }
   }
@@ -546,15 +663,27 @@ acp_status spectral2d_apply(acp_ctx* ctx, const T* X, int ldx, int ncol, const T
   a.kdev = kdev;
   a.kstride = kstride;
   const bool lanczos = Xp != nullptr;
+  const int rpc = 512 / a.px.nt < 16 ? 512 / a.px.nt : 16;  // rows per CTA
+  const int cpc = 512 / a.py.nt < 16 ? 512 / a.py.nt : 16;  // columns per CTA
+  const dim3 grow((ny + rpc - 1) / rpc, npairs), gcol((nx + cpc - 1) / cpc, npairs);
+  const double lg = std::log2((double)N);
+  const size_t fused_smem = (size_t)ny * (nx + 1) * sizeof(T2);
+  if (ctx->opt.fft2d_passes == 0 && fused_smem + 1024 <= ctx->smem_optin) {
+    cudaEvent_t evf = prof_begin(ctx);
+    ::acp::note_launch(ctx);
+    fused2d_kernel<T><<<npairs, 512, fused_smem, ctx->stream>>>(a, X, ldx, twx, twy, mult, V, shift_d, Y, ldy,
+                                                                alpha_d, Xp, ldp, beta_d);
+    ACP_LAUNCH(ctx);
+    prof_end(ctx, sizeof(T) == 8 ? "spectral" : "spectral32", evf, 2.0 * 5.0 * N * lg * npairs + 6.0 * (double)N * ncol,
+             (double)sizeof(T) * N * ncol * (lanczos ? 3.0 : 2.0));
+    return ACP_OK;
+  }
   if (alpha_d) {
     ::acp::note_launch(ctx);
     if (sizeof(T) == 8) zero_kernel_d<<<grid_cap(ncol), 256, 0, ctx->stream>>>(ncol, reinterpret_cast<double*>(alpha_d));
     else zero_kernel_f<<<grid_cap(ncol), 256, 0, ctx->stream>>>(ncol, reinterpret_cast<float*>(alpha_d));
     ACP_LAUNCH(ctx);
   }
-  const int rpc = 512 / a.px.nt < 16 ? 512 / a.px.nt : 16;  // rows per CTA
-  const int cpc = 512 / a.py.nt < 16 ? 512 / a.py.nt : 16;  // columns per CTA
-  const dim3 grow((ny + rpc - 1) / rpc, npairs), gcol((nx + cpc - 1) / cpc, npairs);
   cudaEvent_t ev0 = prof_begin(ctx);
   ::acp::note_launch(ctx);
   rows_fwd_kernel<T><<<grow, rpc * a.px.nt, rpc * nx * sizeof(T2), ctx->stream>>>(a, X, ldx, twx, Z);
@@ -573,7 +702,6 @@ acp_status spectral2d_apply(acp_ctx* ctx, const T* X, int ldx, int ncol, const T
                                                                            kdev, kstride, alpha_d, beta_d, Y, ldy);
     ACP_LAUNCH(ctx);
   }
-  const double lg = std::log2((double)N);
   prof_end(ctx, sizeof(T) == 8 ? "spectral" : "spectral32", ev0, 2.0 * 5.0 * N * lg * npairs + 6.0 * (double)N * ncol,
            (double)sizeof(T) * N * ncol * (lanczos ? 3.0 : 2.0));
   return ACP_OK;
