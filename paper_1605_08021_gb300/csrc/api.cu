@@ -215,7 +215,10 @@ acp_status acp_init(acp_ctx** out, const acp_grid* g, const acp_kernel* k, const
   int N = g->n[0];
   if (g->dim == 1) {
     if (!make_fft_plan(N, &ctx->plan))
-      return fail(set_error(ctx, ACP_E_ARG, "grid size %d must be 2^a 3^b 5^c in [8, 8192]", N));
+      return fail(set_error(ctx, ACP_E_ARG,
+                            "grid size %d is not supported: it must be 2^a 3^b 5^c in [8, 8192] with every radix "
+                            "stage within one CTA of 512 threads (e.g. 5120 = 4^5 5; 6000 = 2^4 3 5^3 is not)",
+                            N));
   } else {
     if (!make_axis_plan(g->n[0], &ctx->plan_x) || !make_axis_plan(g->n[1], &ctx->plan_y))
       return fail(set_error(ctx, ACP_E_ARG, "2D grid sizes %d x %d must be 2^a 3^b 5^c in [8, 4096]", g->n[0],
