@@ -18,9 +18,12 @@ SYSTEMS = ["lat2x2_32_0", "lat2x2_30_1", "latz3x2_36_2"]
 
 
 @pytest.mark.parametrize("name", SYSTEMS)
-def test_hamiltonian_and_kernel_2d(name):
+@pytest.mark.parametrize("passes", [0, 1])
+def test_hamiltonian_and_kernel_2d(name, passes):
+    """Both transforms: one column pair per CTA in shared memory (passes = 0 on these grids) and
+    the row / column passes through device memory (passes = 1)."""
     m = model(name)
-    ctx = context(name)
+    ctx = context(name, fft2d_passes=passes)
     rng = np.random.default_rng(0)
     for ncol in (1, 5, 8):
         X = rng.standard_normal((m.N, ncol))
@@ -45,13 +48,13 @@ def test_perturbations_2d(name):
     assert rel(D2, ref) < 1e-11
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_sternheimer_2d(precision):
+@pytest.mark.parametrize("precision,passes", [(0, 0), (1, 0), (1, 1)])
+def test_sternheimer_2d(precision, passes):
     from oracle.chi0 import sternheimer_operator
     from oracle.minres import minres
     name = "lat2x2_30_1"
     m = model(name)
-    ctx = context(name, stern_tol=1e-12, precision=precision)
+    ctx = context(name, stern_tol=1e-12, precision=precision, fft2d_passes=passes)
     rng = np.random.default_rng(3)
     Bm = rng.standard_normal((m.N, 5))
     shifts = m.eps[rng.integers(0, m.n_orb, 5)]
