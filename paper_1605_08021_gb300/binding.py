@@ -86,6 +86,7 @@ def load():
     P, D, I = c_void_p, POINTER(c_double), c_int
     sig = {
         "acp_options_default": (None, [POINTER(Options)]),
+        "acp_grid_supported": (I, [POINTER(Grid)]),
         "acp_init": (I, [POINTER(P), POINTER(Grid), POINTER(Kernel), P, P, D, I, POINTER(Options), P]),
         "acp_set_options": (I, [P, POINTER(Options)]),
         "acp_apply_chi0": (I, [P, P, I, P, POINTER(Stats)]),
@@ -366,6 +367,17 @@ class Context:
                                          _tptr(Xi), _dptr(rd)))
         k = n_mu.value
         return k, np.array(piv[:k], dtype=np.int64), Xi[:k], rd[:k]
+
+
+def grid_supported(n):
+    """acp_grid_supported: whether a context accepts a grid of n points (an int, 1D) or n = (nx, ny)
+    (2D).  Host only."""
+    g = Grid()
+    if np.ndim(n) == 0:
+        g.dim, g.n[0], g.n[1] = 1, int(n), 1
+    else:
+        g.dim, g.n[0], g.n[1] = 2, int(n[0]), int(n[1])
+    return load().acp_grid_supported(ctypes.byref(g)) == 0
 
 
 def batch_dynamical_matrix(contexts, atoms, rhos, n_workers=0):

@@ -200,6 +200,14 @@ const char* acp_status_string(acp_status s) {
 
 const char* acp_last_error(const acp_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+acp_status acp_grid_supported(const acp_grid* g) {
+  if (!g) return ACP_E_ARG;
+  acp::FftPlan p;
+  if (g->dim == 1) return acp::make_fft_plan(g->n[0], &p) ? ACP_OK : ACP_E_ARG;
+  if (g->dim == 2) return (acp::make_axis_plan(g->n[0], &p) && acp::make_axis_plan(g->n[1], &p)) ? ACP_OK : ACP_E_ARG;
+  return ACP_E_ARG;
+}
+
 acp_status acp_init(acp_ctx** out, const acp_grid* g, const acp_kernel* k, const double* v_eff_d,
                     const double* psi_d, const double* eps_h, int n_orb, const acp_options* opt, void* stream) {
   if (!out || !g || !k || !v_eff_d || !psi_d || !eps_h || !opt) return ACP_E_ARG;
@@ -216,9 +224,7 @@ acp_status acp_init(acp_ctx** out, const acp_grid* g, const acp_kernel* k, const
   if (g->dim == 1) {
     if (!make_fft_plan(N, &ctx->plan))
       return fail(set_error(ctx, ACP_E_ARG,
-                            "grid size %d is not supported: it must be 2^a 3^b 5^c in [8, 8192] with every radix "
-                            "stage within one CTA of 512 threads (e.g. 5120 = 4^5 5; 6000 = 2^4 3 5^3 is not)",
-                            N));
+                            "grid size %d is not supported: it must be 2^a 3^b 5^c in [8, %d]", N, kMaxFftN));
   } else {
     if (!make_axis_plan(g->n[0], &ctx->plan_x) || !make_axis_plan(g->n[1], &ctx->plan_y))
       return fail(set_error(ctx, ACP_E_ARG, "2D grid sizes %d x %d must be 2^a 3^b 5^c in [8, 4096]", g->n[0],

@@ -16,11 +16,15 @@
 namespace acp {
 
 // ---- FFT plan: N = prod rad[s], radices in {2, 3, 4, 5}; threads per transform --------------
+// Largest 1D grid: one FP64 column pair (16 bytes a point) stays within a CTA's shared memory.
+constexpr int kMaxFftN = 10240;
+
 struct FftPlan {
   int n = 0;
   int nst = 0;
   int rad[24];
-  int threads = 0;  // CTA size of the spectral kernels
+  int threads = 0;     // CTA size of the spectral kernels
+  bool wide = false;   // CTAs of up to 1024 threads (grids the 512-thread form does not cover)
 };
 
 bool make_fft_plan(int n, FftPlan* plan);

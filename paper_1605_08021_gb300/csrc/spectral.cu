@@ -71,17 +71,20 @@ __device__ __forceinline__ void dft<5>(double2 (&a)[5], double dir) {
 }
 
 // Butterflies per thread and stage, by radix; the plan sizes the CTA so that these suffice.
-template <int R> struct MaxB;
-template <> struct MaxB<2> { static constexpr int v = 4; };
-template <> struct MaxB<3> { static constexpr int v = 4; };
-template <> struct MaxB<4> { static constexpr int v = 3; };
-template <> struct MaxB<5> { static constexpr int v = 2; };
+// Every grid up to 4096 points fits CTAs of at most 512 threads; the wide form (CTAs of up to
+// 1024 threads, five radix-2 butterflies per thread) covers every 2^a 3^b 5^c grid up to 10240
+// points.  The FP32 kernels use the same counts (one plan serves both).
+template <int R, bool Wide> struct MaxB;
+template <bool W> struct MaxB<2, W> { static constexpr int v = W ? 5 : 4; };
+template <bool W> struct MaxB<3, W> { static constexpr int v = 4; };
+template <bool W> struct MaxB<4, W> { static constexpr int v = 3; };
+template <bool W> struct MaxB<5, W> { static constexpr int v = 2; };
 
 // One in-place Stockham stage: all inputs of the thread are loaded to registers before the CTA
 // barrier, outputs are stored after it.  tw[m] = exp(-2 pi i m / N).
-template <int R>
+template <int R, bool Wide>
 __device__ __noinline__ void fft_stage(double2* s, int N, int Ns, const double2* __restrict__ tw, double dir) {
-  constexpr int B = MaxB<R>::v;
+  constexpr int B = MaxB<R, Wide>::v;
   const int nb = N / R;
   const int stride = N / (Ns * R);
   double2 a[B][R];
@@ -115,6 +118,7 @@ __device__ __noinline__ void fft_stage(double2* s, int N, int Ns, const double2*
 }
 
 constexpr int kMaxThreads = 512;
+constexpr int kMaxThreadsWide = 1024;
 
 struct PlanArg {
   int n, nst;
@@ -122,15 +126,16 @@ struct PlanArg {
 };
 
 // Unnormalised DFT of the N values in shared memory: sum_a s[a] exp(dir 2 pi i a n / N).
+template <bool Wide>
 __device__ void fft(double2* s, const PlanArg& p, const double2* __restrict__ tw, double dir) {
   int Ns = 1;
   for (int st = 0; st < p.nst; ++st) {
     const int R = p.rad[st];
     switch (R) {
-      case 4: fft_stage<4>(s, p.n, Ns, tw, dir); break;
-      case 2: fft_stage<2>(s, p.n, Ns, tw, dir); break;
-      case 3: fft_stage<3>(s, p.n, Ns, tw, dir); break;
-      default: fft_stage<5>(s, p.n, Ns, tw, dir); break;
+      case 4: fft_stage<4, Wide>(s, p.n, Ns, tw, dir); break;
+      case 2: fft_stage<2, Wide>(s, p.n, Ns, tw, dir); break;
+      case 3: fft_stage<3, Wide>(s, p.n, Ns, tw, dir); break;
+      default: fft_stage<5, Wide>(s, p.n, Ns, tw, dir); break;
     }
     Ns *= R;
   }
@@ -144,7 +149,8 @@ PlanArg plan_arg(const FftPlan& p) {
   return a;
 }
 
-__global__ void __launch_bounds__(kMaxThreads) spectral_kernel(const double* __restrict__ X, int ldx, int ncol, PlanArg plan,
+template <bool Wide>
+__global__ void __launch_bounds__(Wide ? kMaxThreadsWide : kMaxThreads) spectral_kernel(const double* __restrict__ X, int ldx, int ncol, PlanArg plan,
                                 const double2* __restrict__ tw, const double* __restrict__ mult,
                                 const double* __restrict__ V, const double* __restrict__ shift,
                                 double* __restrict__ Y, int ldy, double* __restrict__ alpha,
@@ -162,10 +168,10 @@ __global__ void __launch_bounds__(kMaxThreads) spectral_kernel(const double* __r
   for (int a = threadIdx.x; a < N; a += blockDim.x)
     sbuf[a] = make_double2(act0 ? x0[a] : 0.0, act1 ? x1[a] : 0.0);
   __syncthreads();
-  fft(sbuf, plan, tw, -1.0);
+  fft<Wide>(sbuf, plan, tw, -1.0);
   for (int a = threadIdx.x; a < N; a += blockDim.x) sbuf[a] = cscale(sbuf[a], __ldg(&mult[a]));
   __syncthreads();
-  fft(sbuf, plan, tw, 1.0);
+  fft<Wide>(sbuf, plan, tw, 1.0);
   const double invN = 1.0 / N;
   const double sh0 = (shift && act0) ? shift[c0] : 0.0;
   const double sh1 = (shift && act1) ? shift[c1] : 0.0;
@@ -221,7 +227,8 @@ __device__ __forceinline__ double2 pseudo_coeff(int n, double L, double Z, doubl
 }
 
 // One CTA per atom: G[:, I] + i B[:, I] from one inverse transform, D2[:, I] from a second.
-__global__ void __launch_bounds__(kMaxThreads) perturbation_kernel(PlanArg plan, const double2* __restrict__ tw, double L, double kappa,
+template <bool Wide>
+__global__ void __launch_bounds__(Wide ? kMaxThreadsWide : kMaxThreads) perturbation_kernel(PlanArg plan, const double2* __restrict__ tw, double L, double kappa,
                                     double scale, const double* __restrict__ R, const double* __restrict__ Z,
                                     const double* __restrict__ sig, double* G, double* B, double* D2) {
   extern __shared__ double2 sbuf[];
@@ -242,7 +249,7 @@ __global__ void __launch_bounds__(kMaxThreads) perturbation_kernel(PlanArg plan,
       sbuf[a] = make_double2(gh.x - bh.y, gh.y + bh.x);
     }
     __syncthreads();
-    fft(sbuf, plan, tw, 1.0);
+    fft<Wide>(sbuf, plan, tw, 1.0);
     for (int a = threadIdx.x; a < N; a += blockDim.x) {
       if (G) G[(size_t)I * N + a] = sbuf[a].x * invL;
       if (B) B[(size_t)I * N + a] = sbuf[a].y * invL;
@@ -257,7 +264,7 @@ __global__ void __launch_bounds__(kMaxThreads) perturbation_kernel(PlanArg plan,
       sbuf[a] = cscale(pseudo_coeff(n, L, ZI, sI, RI), -k * k * khat);
     }
     __syncthreads();
-    fft(sbuf, plan, tw, 1.0);
+    fft<Wide>(sbuf, plan, tw, 1.0);
     for (int a = threadIdx.x; a < N; a += blockDim.x) D2[(size_t)I * N + a] = sbuf[a].x * invL;
   }
 }
@@ -271,8 +278,10 @@ acp_status spectral_configure(acp_ctx* ctx) {
   std::lock_guard<std::mutex> lock(device_mutex());
   static int configured_device = -1;
   if (configured_device == ctx->device) return ACP_OK;
-  ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(spectral_kernel)));
-  ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(perturbation_kernel)));
+  ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(spectral_kernel<false>)));
+  ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(spectral_kernel<true>)));
+  ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(perturbation_kernel<false>)));
+  ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(perturbation_kernel<true>)));
   configured_device = ctx->device;
   return ACP_OK;
 }
@@ -288,7 +297,7 @@ acp_status raise_smem_limit(acp_ctx* ctx, const void* func) {
 }
 
 bool make_fft_plan(int n, FftPlan* plan) {
-  if (n < 8 || n > 8192) return false;
+  if (n < 8 || n > kMaxFftN) return false;
   FftPlan p{};
   p.n = n;
   int m = n;
@@ -298,18 +307,26 @@ bool make_fft_plan(int n, FftPlan* plan) {
   while (m % 3 == 0) push(3);
   while (m % 5 == 0) push(5);
   if (m != 1 || p.nst > 24) return false;
-  int t = 64;
-  for (int s = 0; s < p.nst; ++s) {
-    const int r = p.rad[s];
-    const int mb = (r == 2) ? 4 : (r == 3) ? 4 : (r == 4) ? 3 : 2;
-    const int need = (n / r + mb - 1) / mb;
-    if (need > t) t = need;
+  // the smallest CTA (a multiple of 32 threads, at least 64) in which every stage's butterflies
+  // fit the per-thread counts MaxB of the narrow form, else of the wide form
+  for (int wide = 0; wide < 2; ++wide) {
+    int t = 64;
+    for (int s = 0; s < p.nst; ++s) {
+      const int r = p.rad[s];
+      const int mb = (r == 2) ? (wide ? MaxB<2, true>::v : MaxB<2, false>::v) : (r == 3) ? MaxB<3, false>::v
+                     : (r == 4) ? MaxB<4, false>::v : MaxB<5, false>::v;
+      const int need = (n / r + mb - 1) / mb;
+      if (need > t) t = need;
+    }
+    t = (t + 31) / 32 * 32;
+    if (t <= (wide ? kMaxThreadsWide : kMaxThreads)) {
+      p.threads = t;
+      p.wide = wide != 0;
+      *plan = p;
+      return true;
+    }
   }
-  t = (t + 31) / 32 * 32;
-  if (t > 512) return false;  // kMaxThreads of the spectral kernels
-  p.threads = t;
-  *plan = p;
-  return true;
+  return false;
 }
 
 acp_status spectral_apply(acp_ctx* ctx, const double* X, int ldx, int ncol, SpectralMult mult, bool with_v,
@@ -323,7 +340,8 @@ acp_status spectral_apply(acp_ctx* ctx, const double* X, int ldx, int ncol, Spec
   const int blocks = (ncol + 1) / 2;
   ::acp::note_launch(ctx);
   cudaEvent_t ev0 = prof_begin(ctx);
-  spectral_kernel<<<blocks, ctx->plan.threads, ctx->N * sizeof(double2), ctx->stream>>>(
+  auto kernel = ctx->plan.wide ? spectral_kernel<true> : spectral_kernel<false>;
+  kernel<<<blocks, ctx->plan.threads, ctx->N * sizeof(double2), ctx->stream>>>(
       X, ldx, ncol, plan_arg(ctx->plan), ctx->d_tw, m, with_v ? ctx->d_V : nullptr, shift_d, Y, ldy, alpha_d,
       active_d, Xprev, beta_d);
   ACP_LAUNCH(ctx);
@@ -342,7 +360,8 @@ acp_status perturbations_1d(acp_ctx* ctx, int n_atoms, const double* R_d, const 
                             double* G, double* B, double* D2) {
   if (n_atoms <= 0) return ACP_OK;
   ::acp::note_launch(ctx);
-  perturbation_kernel<<<n_atoms, ctx->plan.threads, ctx->N * sizeof(double2), ctx->stream>>>(
+  auto kernel = ctx->plan.wide ? perturbation_kernel<true> : perturbation_kernel<false>;
+  kernel<<<n_atoms, ctx->plan.threads, ctx->N * sizeof(double2), ctx->stream>>>(
       plan_arg(ctx->plan), ctx->d_tw, ctx->L, ctx->kappa, ctx->scale, R_d, Z_d, sig_d, G, B, D2);
   ACP_LAUNCH(ctx);
   return ACP_OK;

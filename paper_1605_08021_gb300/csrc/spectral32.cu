@@ -67,15 +67,15 @@ __device__ __forceinline__ void dftf<5>(float2 (&a)[5], float dir) {
   a[3] = csubf(m2, e2);
 }
 
-template <int R> struct MaxBf;
-template <> struct MaxBf<2> { static constexpr int v = 4; };
-template <> struct MaxBf<3> { static constexpr int v = 4; };
-template <> struct MaxBf<4> { static constexpr int v = 3; };
-template <> struct MaxBf<5> { static constexpr int v = 2; };
+template <int R, bool Wide> struct MaxBf;
+template <bool W> struct MaxBf<2, W> { static constexpr int v = W ? 5 : 4; };
+template <bool W> struct MaxBf<3, W> { static constexpr int v = 4; };
+template <bool W> struct MaxBf<4, W> { static constexpr int v = 3; };
+template <bool W> struct MaxBf<5, W> { static constexpr int v = 2; };
 
-template <int R>
+template <int R, bool Wide>
 __device__ __forceinline__ void fft_stage_f(float2* s, int N, int Ns, const float2* __restrict__ tw, float dir) {
-  constexpr int B = MaxBf<R>::v;
+  constexpr int B = MaxBf<R, Wide>::v;
   const int nb = N / R;
   const int stride = N / (Ns * R);
   float2 a[B][R];
@@ -113,14 +113,15 @@ struct PlanArgF {
   int rad[24];
 };
 
+template <bool Wide>
 __device__ void fft_f(float2* s, const PlanArgF& p, const float2* __restrict__ tw, float dir) {
   int Ns = 1;
   for (int st = 0; st < p.nst; ++st) {
     switch (p.rad[st]) {
-      case 4: fft_stage_f<4>(s, p.n, Ns, tw, dir); break;
-      case 2: fft_stage_f<2>(s, p.n, Ns, tw, dir); break;
-      case 3: fft_stage_f<3>(s, p.n, Ns, tw, dir); break;
-      default: fft_stage_f<5>(s, p.n, Ns, tw, dir); break;
+      case 4: fft_stage_f<4, Wide>(s, p.n, Ns, tw, dir); break;
+      case 2: fft_stage_f<2, Wide>(s, p.n, Ns, tw, dir); break;
+      case 3: fft_stage_f<3, Wide>(s, p.n, Ns, tw, dir); break;
+      default: fft_stage_f<5, Wide>(s, p.n, Ns, tw, dir); break;
     }
     Ns *= p.rad[st];
   }
@@ -146,14 +147,17 @@ __device__ __forceinline__ float block_sum_f(float v, float* red) {
 }
 
 constexpr int kMaxThreads = 512;
+constexpr int kMaxThreadsWide = 1024;  // grids beyond the 512-thread plan (see the FP64 kernels)
 
 // P = (H - s_j) x_j - alpha_j x_j - beta_j xp_j with alpha_j = x_j . (H - s_j) x_j (Lanczos form,
 // xp != nullptr), or Y = (H - s_j) x_j.  shift (nullable) per column; active (nullable) masks
 // columns; alpha (nullable) receives the coefficients.
 // Two CTAs per SM (64 registers per thread, a few spilled): the FFT stages wait on shared and L1
 // loads behind CTA barriers, and a second resident CTA hides them (33% faster than one CTA of
-// 120 registers on the 64-atom chain).
-__global__ void __launch_bounds__(kMaxThreads, 2)
+// 120 registers on the 64-atom chain).  The wide form runs one CTA of up to 1024 threads per SM,
+// with the same 64 registers per thread.
+template <bool Wide>
+__global__ void __launch_bounds__(Wide ? kMaxThreadsWide : kMaxThreads, Wide ? 1 : 2)
     spectral32_kernel(const float* __restrict__ X, int ldx, int ncol, PlanArgF plan, const float2* __restrict__ tw,
                       const float* __restrict__ kin, const float* __restrict__ V, const float* __restrict__ shift,
                       float* __restrict__ Y, int ldy, float* __restrict__ alpha, const int* __restrict__ active,
@@ -178,10 +182,10 @@ __global__ void __launch_bounds__(kMaxThreads, 2)
   for (int a = threadIdx.x; a < N; a += blockDim.x)
     sbuf32[a] = make_float2(act0 ? x0[a] : 0.f, act1 ? x1[a] : 0.f);
   __syncthreads();
-  fft_f(sbuf32, plan, tw, -1.f);
+  fft_f<Wide>(sbuf32, plan, tw, -1.f);
   for (int a = threadIdx.x; a < N; a += blockDim.x) sbuf32[a] = cscalef(sbuf32[a], __ldg(&kin[a]));
   __syncthreads();
-  fft_f(sbuf32, plan, tw, 1.f);
+  fft_f<Wide>(sbuf32, plan, tw, 1.f);
   const float invN = 1.f / N;
   const float sh0 = (shift && act0) ? shift[c0] : 0.f;
   const float sh1 = (shift && act1) ? shift[c1] : 0.f;
@@ -252,7 +256,8 @@ acp_status tables32(acp_ctx* ctx, const float** kin32, const float** V32, const 
     std::lock_guard<std::mutex> lock(device_mutex());
     static int configured_device = -1;
     if (configured_device != ctx->device) {
-      ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(spectral32_kernel)));
+      ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(spectral32_kernel<false>)));
+      ACP_TRY(raise_smem_limit(ctx, reinterpret_cast<const void*>(spectral32_kernel<true>)));
       configured_device = ctx->device;
     }
     ctx->tables32_stale = false;
@@ -280,7 +285,8 @@ acp_status spectral32_apply(acp_ctx* ctx, const float* X, int ldx, int ncol, con
   const int blocks = (ncol + 1) / 2;
   ::acp::note_launch(ctx);
   cudaEvent_t ev0 = prof_begin(ctx);
-  spectral32_kernel<<<blocks, ctx->plan.threads, ctx->N * sizeof(float2), ctx->stream>>>(
+  auto kernel = ctx->plan.wide ? spectral32_kernel<true> : spectral32_kernel<false>;
+  kernel<<<blocks, ctx->plan.threads, ctx->N * sizeof(float2), ctx->stream>>>(
       X, ldx, ncol, pa, tw, kin, V, shift_d, Y, ldy, alpha_d, active_d, Xprev, ldp, beta_d, kdev, kstride);
   ACP_LAUNCH(ctx);
   const double lg = std::log2((double)ctx->N);

@@ -15,6 +15,11 @@ def system(name):
         s = W.config(2)
     elif name == "c3":
         s = W.config(3)
+    elif name.startswith("c4_"):
+        # system <i> of the 64 batched chains (ground state from the cached potential, as the
+        # benchmark loads it)
+        s = W.batch_config(4)[int(name[3:])]
+        return s, W.ground_state(s, tol=1e-4)
     elif name.startswith("small"):
         # small<atoms>_<grid>_<seed>
         a, n, seed = (int(x) for x in name[5:].split("_"))
@@ -38,7 +43,7 @@ def model(name):
     return Model2D(s, gs) if s.dim == 2 else Model1D(s, gs)
 
 
-def context(name, **opts):
+def context(name, stream=None, **opts):
     import torch
 
     import paper_1605_08021_gb300 as P
@@ -47,7 +52,7 @@ def context(name, **opts):
     psi = torch.tensor(np.ascontiguousarray(gs.psi.T), dtype=torch.float64, device="cuda")
     o = P.options(occ=float(s.occ), **opts)
     n, L = (s.n, s.L) if s.dim == 2 else (s.n[0], s.L[0])
-    ctx = P.Context(n, L, s.kappa, s.scale, V, psi, gs.eps[: gs.n_orb], o)
+    ctx = P.Context(n, L, s.kappa, s.scale, V, psi, gs.eps[: gs.n_orb], o, stream=stream)
     return ctx
 
 

@@ -54,3 +54,23 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     out = ctypes.c_void_p()
     assert lib.acp_init(ctypes.byref(out), None, None, None, None, None, 0, None, None) == 1
     assert lib.acp_apply_chi0(None, None, 0, None, None) == 1
+
+
+def _smooth(n):
+    for r in (2, 3, 5):
+        while n % r == 0:
+            n //= r
+    return n == 1
+
+
+def test_grid_support_bounds(lib):
+    """Every 2^a 3^b 5^c grid in [8, 10240] is accepted in 1D (the plans that need CTAs of more than
+    512 threads take the wide form of the spectral kernels), nothing else is; 2D axes up to 4096."""
+    for n in range(1, 10300):
+        assert P.grid_supported(n) == (8 <= n <= 10240 and _smooth(n)), n
+    assert P.grid_supported((160, 160)) and P.grid_supported((4096, 8))
+    assert not P.grid_supported((4320, 8)) and not P.grid_supported((160, 7))
+    g = B.Grid()
+    g.dim = 3
+    assert lib.acp_grid_supported(ctypes.byref(g)) == 1
+    assert lib.acp_grid_supported(None) == 1
