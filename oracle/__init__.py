@@ -14,4 +14,6 @@ Modules
   dyson   u = chi g from the Dyson equation (Eq. dyson) by GMRES or by a dense solve.
   dmat    dynamical matrix (Eq. SecDeriv) and phonon frequencies.
   acp     the compression of Alg. 2 (Remark variant), Alg. 3 and the adaptive Alg. 4.
+  cnn     the learned initial guess of the 2D Sternheimer solves: a 4-layer periodic CNN,
+          its backward pass, bfloat16 weight rounding and Adam.
 """
