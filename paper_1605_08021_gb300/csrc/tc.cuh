@@ -53,12 +53,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete; false if the deadline passed first.
+// Wait for the phase with the given parity to complete; false if the deadline passed first, or
+// after 2^28 polls should the timer not advance (a poll takes at least a few nanoseconds, so the
+// cap lies beyond any deadline used here).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t deadline_ns) {
-  for (uint32_t i = 0;; ++i) {
+  constexpr uint32_t kMaxPolls = 1u << 28;
+  for (uint32_t i = 0; i < kMaxPolls; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 63u) == 63u && globaltimer_ns() > deadline_ns) return false;
   }
+  return false;
 }
 
 // ---- TMA --------------------------------------------------------------------------------------

@@ -102,12 +102,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       bool ok = true;
+      int issued = 0;
       for (int i = 0; i < nkb; ++i) {
         const int s = i % kStages, u = i / kStages;
         if (u > 0 && !tc::mbar_wait(&empty_bar[s], (u - 1) & 1, deadline)) {
           ok = false;
           break;
         }
+        ++issued;
         uint8_t* st = base + s * stage_bytes;
         tc::mbar_arrive_expect_tx(&full_bar[s], (p.split_a ? a_bytes : 2 * a_bytes) + 2 * b_bytes);
         const int kx = (kb0 + i) * kBK;
@@ -116,6 +118,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::tma_load_2d(st + 2 * a_bytes, &mBhi, &full_bar[s], kx, n0);
         tc::tma_load_2d(st + 2 * a_bytes + b_bytes, &mBlo, &full_bar[s], kx, n0);
       }
+      // no copy may still be landing in shared memory when the CTA exits: wait (bounded) for the
+      // last load of every stage; each load completes its stage's full barrier once, so the
+      // phase of load i is i / kStages (already complete on the normal path)
+      const uint64_t drain = tc::globaltimer_ns() + kWaitNs;
+      for (int i = issued > kStages ? issued - kStages : 0; i < issued; ++i)
+        if (!tc::mbar_wait(&full_bar[i % kStages], (uint32_t)(i / kStages) & 1u, drain)) ok = false;
       if (!ok) atomicExch(&abort_sh, 1);
     }
   } else if (warp == 1) {
@@ -214,6 +222,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   if (warp == 1) {
     tc::tc_fence_after();
+    // the MMAs must be done with the accumulator before it is freed (complete on the normal
+    // path, where the epilogue has waited for the same phase)
+    if (!tc::mbar_wait(&done_bar, 0, tc::globaltimer_ns() + kWaitNs) && lane == 0) atomicExch(p.status, 1);
     tc::tmem_dealloc(tmem, p.tmem_cols);
   }
   if (threadIdx.x == 0 && abort_sh) atomicExch(p.status, 1);

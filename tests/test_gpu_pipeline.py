@@ -133,6 +133,21 @@ def test_error_statuses():
     assert U.shape == (0, m.N)
 
 
+def test_deadline_returns_timeout_status():
+    """deadline_s is checked on the host between launches (every 16 MINRES steps here): a call that
+    overruns it returns ACP_E_TIMEOUT with its kernels finished, and the context stays usable."""
+    import paper_1605_08021_gb300 as P
+    name = "small4_160_0"
+    m = model(name)
+    G, _ = m.perturbations()
+    ctx = context(name, method=0, deadline_s=1e-9)
+    with pytest.raises(P.AcpError) as e:
+        ctx.apply_chi0(to_gpu(G[:, :2]))
+    assert e.value.name == "ACP_E_TIMEOUT"
+    Y = to_np(ctx.hamiltonian_apply(to_gpu(G[:, :2])))
+    assert rel(Y, m.apply_H(G[:, :2])) < 1e-12
+
+
 def test_multishift_storage_variants_agree():
     """The stored-basis multi-shift solver and the per-shift-vector solver give the same chi0~ G."""
     name = "small6_240_1"
