@@ -54,6 +54,9 @@ enum { ACP_METHOD_PLAIN = 0, ACP_METHOD_ACP = 1 };
    compression, the Dyson update, D and its eigenvalues stay in FP64. */
 enum { ACP_PREC_FP64 = 0, ACP_PREC_MIXED = 1 };
 
+/* Weights of the learned initial guess (see acp_cnn_set_weights). */
+enum { ACP_CNN_WEIGHTS = 19393 };
+
 /* Periodic grid.  dim = 1: n[0] points on [0, L[0]), n[0] = 2^a 3^b 5^c in [8, 10240] (one
    transform per CTA; some grids above 4096 points use CTAs of up to 1024 threads).  dim = 2:
    n[0] x n[1] points on [0, L[0]) x [0, L[1]), each n = 2^a 3^b 5^c in [8, 4096]; grid functions are flattened with x
@@ -118,6 +121,11 @@ typedef struct {
   int fft2d_passes;    /* 2D grids: 0 transforms a column pair inside one CTA's shared memory when
                           it fits, else in row / column passes through device memory; 1 always
                           uses the passes.                                                          */
+  int learned;         /* 2D grids, mixed precision: 1 starts every single-shift Sternheimer solve
+                          (Alg. 1 columns, acp_sternheimer_solve) from Q x0 with x0 the learned
+                          initial guess (acp_cnn_set_weights must have been called); 0 from zero.
+                          The solves refine to stern_tol either way.  The multi-shift solves of
+                          Alg. 3 share one Krylov space across shifts and start from zero.        */
 } acp_options;
 
 typedef struct {
@@ -235,6 +243,25 @@ acp_status acp_compress(acp_ctx* ctx, const double* G_d, int ncol, int cap, int*
 /* Replace the ground state of an existing context (same grid, kernel and n_orb), reusing its
    device workspace: v_eff_d, psi_d device (N and N x n_orb), eps_h host (n_orb, ascending). */
 acp_status acp_update(acp_ctx* ctx, const double* v_eff_d, const double* psi_d, const double* eps_h, int n_orb);
+
+/* ---- learned initial guess (no counterpart in the paper) -------------------------------- */
+
+/* Set the weights of the network that proposes initial guesses for 2D Sternheimer solves:
+   x0 = rms(r) net(r / rms(r), V_eff - s) for a right-hand side r and shift s, with
+   rms(r) = sqrt(mean(r^2)) (x0 = 0 for r = 0), and net a 4-layer periodic CNN on the nx x ny grid:
+   3 x 3 cross-correlations (z_o[y, x] = b_o + sum_c sum_{p,q in -1..1} W[o, c, p+1, q+1]
+   a_c[(y+p) mod ny, (x+q) mod nx]), channels 2 -> 32 -> 32 -> 32 -> 1, tanh after layers 1-3.
+   w_h: host, n = ACP_CNN_WEIGHTS FP32 values, in the order W1 (32,2,3,3), b1 (32), W2 (32,32,3,3),
+   b2 (32), W3 (32,32,3,3), b3 (32), W4 (1,32,3,3), b4 (1), each row-major; input channel 0 is r /
+   rms(r), channel 1 is V_eff - s.  The context keeps an FP32 copy and convolves with bfloat16
+   copies (round to nearest even) in FP32 arithmetic.  The call returns once w_h may be reused.
+   Errors: ACP_E_ARG (null, n != ACP_CNN_WEIGHTS, not a 2D context), ACP_E_CUDA, ACP_E_OOM. */
+acp_status acp_cnn_set_weights(acp_ctx* ctx, const float* w_h, long long n);
+
+/* X0_d[:, j] = rms(R_j) net(R_j / rms(R_j), V_eff - shift_h[j]) for every column j (not
+   projected).  R_d, X0_d: device, N x ncol (N = nx ny, x fastest); shift_h: host, ncol values.
+   Errors: ACP_E_ARG (no weights, not a 2D context, bad pointers), ACP_E_CUDA. */
+acp_status acp_cnn_apply(acp_ctx* ctx, const double* R_d, int ncol, const double* shift_h, double* X0_d);
 
 /* ---- projector without device allocation (no counterpart in the paper) ------------------ */
 

@@ -22,6 +22,7 @@ ACP_METHOD_PLAIN = 0
 ACP_METHOD_ACP = 1
 ACP_PREC_FP64 = 0
 ACP_PREC_MIXED = 1
+ACP_CNN_WEIGHTS = 19393
 
 STATUS = {0: "ACP_OK", 1: "ACP_E_ARG", 2: "ACP_E_CUDA", 3: "ACP_E_OOM", 4: "ACP_E_NOCONV",
           5: "ACP_E_TIMEOUT", 6: "ACP_E_GAP", 7: "ACP_E_RANK", 8: "ACP_E_NUMERIC"}
@@ -53,7 +54,7 @@ class Options(ctypes.Structure):
                 ("stern_tol", c_double), ("stern_maxit", c_int), ("dyson_tol", c_double),
                 ("dyson_maxit", c_int), ("rhs_batch", c_int), ("deadline_s", c_double),
                 ("project_every", c_int), ("ms_variant", c_int), ("precision", c_int),
-                ("use_graphs", c_int), ("fft2d_passes", c_int)]
+                ("use_graphs", c_int), ("fft2d_passes", c_int), ("learned", c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -103,6 +104,8 @@ def load():
         "acp_kernel_apply": (I, [P, P, I, I, P]),
         "acp_sternheimer_solve": (I, [P, P, I, D, P, POINTER(Stats)]),
         "acp_compress": (I, [P, P, I, I, POINTER(c_int), POINTER(c_int), P, D]),
+        "acp_cnn_set_weights": (I, [P, POINTER(ctypes.c_float), c_longlong]),
+        "acp_cnn_apply": (I, [P, P, I, D, P]),
         "acp_update": (I, [P, P, P, D, I]),
         "acp_profile_enable": (I, [P, I]),
         "acp_profile_get": (I, [P, ctypes.c_char_p, D, POINTER(c_longlong), D, D]),
@@ -137,13 +140,13 @@ def _check_block(t, N, name):
 
 def options(method=ACP_METHOD_ACP, occ=1.0, n_cheb=16, id_tol=1e-5, sketch=None, max_rank=0,
             stern_tol=1e-11, stern_maxit=5000, dyson_tol=1e-10, dyson_maxit=30, rhs_batch=0,
-            deadline_s=0.0, project_every=0, ms_variant=0, precision=0, use_graphs=0, fft2d_passes=0):
+            deadline_s=0.0, project_every=0, ms_variant=0, precision=0, use_graphs=0, fft2d_passes=0, learned=0):
     """Options as a dict (the sketch Omega, if given, is an (n_cols, r) float64 array)."""
     return dict(method=method, occ=occ, n_cheb=n_cheb, id_tol=id_tol, sketch=sketch, max_rank=max_rank,
                 stern_tol=stern_tol, stern_maxit=stern_maxit, dyson_tol=dyson_tol, dyson_maxit=dyson_maxit,
                 rhs_batch=rhs_batch, deadline_s=deadline_s, project_every=project_every,
                 ms_variant=ms_variant, precision=precision, use_graphs=use_graphs,
-                fft2d_passes=fft2d_passes)
+                fft2d_passes=fft2d_passes, learned=learned)
 
 
 class Context:
@@ -218,6 +221,7 @@ class Context:
         o.precision = int(d.get("precision", 0))
         o.use_graphs = int(d.get("use_graphs", 0))
         o.fft2d_passes = int(d.get("fft2d_passes", 0))
+        o.learned = int(d.get("learned", 0))
         self._opts = o
         return o
 
@@ -345,6 +349,21 @@ class Context:
         Y = self._out(X.shape[0])
         self._call(self.lib.acp_kernel_apply(self.ptr, _tptr(X), X.shape[0], -1 if inverse else 1, _tptr(Y)))
         return Y
+
+    def cnn_set_weights(self, w):
+        """acp_cnn_set_weights: w is the packed weight vector (ACP_CNN_WEIGHTS values)."""
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float32).ravel())
+        self._call(self.lib.acp_cnn_set_weights(self.ptr, w.ctypes.data_as(POINTER(ctypes.c_float)), w.size))
+
+    def cnn_apply(self, R, shifts):
+        """acp_cnn_apply: learned initial guesses for the columns of R (rows of the tensor)."""
+        _check_block(R, self.N, "R")
+        X0 = self._out(R.shape[0])
+        sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+        if sh.shape != (R.shape[0],):
+            raise ValueError("one shift per column")
+        self._call(self.lib.acp_cnn_apply(self.ptr, _tptr(R), R.shape[0], _dptr(sh), _tptr(X0)))
+        return X0
 
     def sternheimer_solve(self, Bm, shifts, allow_noconv=False):
         _check_block(Bm, self.N, "B")

@@ -136,6 +136,7 @@ acp_status validate_options(acp_ctx* ctx, const acp_options* o) {
   if (o->ms_variant < 0 || o->ms_variant > 2) return set_error(ctx, ACP_E_ARG, "ms_variant must be 0, 1 or 2");
   if (o->precision != ACP_PREC_FP64 && o->precision != ACP_PREC_MIXED)
     return set_error(ctx, ACP_E_ARG, "unknown precision %d", o->precision);
+  if (o->learned != 0 && o->learned != 1) return set_error(ctx, ACP_E_ARG, "learned must be 0 or 1");
   return ACP_OK;
 }
 
@@ -580,6 +581,26 @@ acp_status acp_sternheimer_solve(acp_ctx* ctx, const double* B_d, int ncol, cons
   ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   fill_stats(stats, rep, t0);
   if (!rep.all_converged) return set_error(ctx, ACP_E_NOCONV, "MINRES hit the iteration cap");
+  return ACP_OK;
+}
+
+acp_status acp_cnn_set_weights(acp_ctx* ctx, const float* w_h, long long n) {
+  ACP_TRY(check_ctx(ctx));
+  if (!w_h || n != ACP_CNN_WEIGHTS)
+    return set_error(ctx, ACP_E_ARG, "expected %d weights, got %lld", (int)ACP_CNN_WEIGHTS, n);
+  if (ctx->dim != 2) return set_error(ctx, ACP_E_ARG, "the learned initial guess is defined on 2D grids");
+  return cnn_set_weights(ctx, w_h);
+}
+
+acp_status acp_cnn_apply(acp_ctx* ctx, const double* R_d, int ncol, const double* shift_h, double* X0_d) {
+  ACP_TRY(check_ctx(ctx));
+  if (ncol == 0) return ACP_OK;
+  if (!R_d || !X0_d || !shift_h || ncol < 0) return set_error(ctx, ACP_E_ARG, "bad arguments");
+  double* sh = nullptr;
+  ACP_TRY(ws(ctx, "cnn_shift", ncol, &sh));
+  ACP_CUDA(ctx, cudaMemcpyAsync(sh, shift_h, sizeof(double) * ncol, cudaMemcpyHostToDevice, ctx->stream));
+  ACP_TRY(cnn_initial_guess(ctx, R_d, ctx->N, ncol, sh, X0_d, ctx->N));
+  ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // shift_h may go away
   return ACP_OK;
 }
 

@@ -94,6 +94,7 @@ struct acp_ctx {
   std::map<long long, std::pair<int, int>> tc_tune;  // projector tile choice per shape
   bool mixed_refine = true;       // mixed precision: refine the multi-shift solves to stern_tol
   long long graph_launch_nodes = 0;  // kernels replayed through CUDA graphs (launch counter)
+  bool cnn_ready = false;         // weights of the learned initial guess are set (2D)
   acp::FftPlan plan;
   acp::Workspace ws;
   acp::Profiler prof;
@@ -241,6 +242,13 @@ acp_status mixed_prepare(acp_ctx* ctx);
 acp_status project32(acp_ctx* ctx, const float* X, int ldx, int ncol, float* Y, int ldy);
 acp_status tc_check(acp_ctx* ctx);
 acp_status project_mixed64(acp_ctx* ctx, const double* X, int ncol, double* Y);
+
+// cnn.cu: the learned initial guess of the 2D Sternheimer solves.  cnn_set_weights copies the
+// packed FP32 weights (host) and builds the bfloat16 copies; cnn_initial_guess writes
+// X0 = rms(R_j) net(R_j / rms(R_j), V_eff - shift_j) per column (not projected).
+acp_status cnn_set_weights(acp_ctx* ctx, const float* w_h);
+acp_status cnn_initial_guess(acp_ctx* ctx, const double* R, int ldr, int ncol, const double* shift_d, double* X0,
+                             int ldx);
 
 // dense.cu: LU solve of an n x n system with nrhs right-hand sides (A, B overwritten; X in B).
 acp_status lu_solve(acp_ctx* ctx, double* A, int n, double* B, int nrhs);

@@ -647,6 +647,12 @@ acp_status refine(acp_ctx* ctx, const double* B, int ncol, const double* shift_d
 acp_status minres_batched_mixed(acp_ctx* ctx, const double* B, int ncol, const double* shift_d, double* X,
                                 SolveReport* rep, double t0_ms) {
   if (ncol <= 0) return ACP_OK;
+  if (ctx->opt.learned && ctx->dim == 2) {
+    // start from the learned guess, projected onto range(Q) where the solution lies
+    ACP_TRY(cnn_initial_guess(ctx, B, ctx->N, ncol, shift_d, X, ctx->N));
+    ACP_TRY(project(ctx, X, ctx->N, ncol, X, ctx->N));
+    return refine(ctx, B, ncol, shift_d, X, false, rep, t0_ms);
+  }
   return refine(ctx, B, ncol, shift_d, X, true, rep, t0_ms);
 }
 

@@ -24,6 +24,13 @@ def system(name):
         # small<atoms>_<grid>_<seed>
         a, n, seed = (int(x) for x in name[5:].split("_"))
         s = W.small_chain(a, n, seed)
+    elif name.startswith("rect"):
+        # rect<nxa>x<nya>_<nx>x<ny>_<seed>: a small lattice on a grid with nx != ny
+        dims, grid, seed = name[4:].split("_")
+        nxa, nya = (int(x) for x in dims.split("x"))
+        gx, gy = (int(x) for x in grid.split("x"))
+        s = W.small_lattice(nxa, nya, gx, int(seed))
+        s = W.System(**{**s.__dict__, "name": s.name + f"_{gx}x{gy}", "n": (gx, gy)})
     elif name.startswith("lat"):
         # lat<nx>x<ny>_<grid>_<seed>: small 2D lattices (spacing 8 bohr, mixed Z, occupation 1);
         # latz...: all Z = 2, occupation 2 (closed shells)

@@ -1,0 +1,87 @@
+"""The learned initial guess of the 2D Sternheimer solves (4-layer periodic CNN, bfloat16 weights,
+FP32 activations and accumulation) against the oracle's network (``oracle/cnn.py``) evaluated in
+FP64 on the same bfloat16-rounded weights.
+
+Bar for the network output: the device rounds its inputs to FP32 (relative 6e-8), accumulates
+each of its 32-channel layers over 288 products in FP32 (~sqrt(288) x 6e-8 ~ 1e-6 relative per
+layer) and evaluates tanh in FP32; over four layers of unit gain that stays below 2e-5 relative.
+Solves started from the guess refine to the same tolerance as solves started from zero, so the
+solutions agree to the Krylov bar of the other 2D tests (1e-8).
+
+Grids: 32 x 32 (two full tiles of 16 per axis), 30 x 30 and 36 x 36 (ragged last tiles), and
+40 x 24 (nx != ny, ragged in both directions).
+"""
+import numpy as np
+import pytest
+
+import acp_workloads as W
+from gpu_systems import context, model, rel, to_gpu, to_np
+
+pytestmark = pytest.mark.gpu
+
+SYSTEMS = ["lat2x2_32_0", "lat2x2_30_1", "latz3x2_36_2", "rect2x2_40x24_0"]
+
+
+@pytest.mark.parametrize("name", SYSTEMS)
+def test_cnn_apply_matches_oracle(name):
+    from oracle import cnn as C
+    m = model(name)
+    ctx = context(name)
+    w = W.learned.init_weights(1)
+    ctx.cnn_set_weights(w)
+    params = W.learned.unpack(w)
+    rng = np.random.default_rng(30)
+    R = rng.standard_normal((m.N, 4))
+    R[:, 2] = 0.0
+    shifts = m.eps[rng.integers(0, m.n_orb, 4)]
+    X0 = to_np(ctx.cnn_apply(to_gpu(R), shifts))
+    for j in range(4):
+        ref = C.forward(params, R[:, j].reshape(m.ny, m.nx), (m.V - shifts[j]).reshape(m.ny, m.nx),
+                        bf16=True).reshape(-1)
+        if j == 2:
+            assert not np.any(X0[:, j])
+        else:
+            assert rel(X0[:, j], ref) < 2e-5, j
+
+
+def test_learned_start_gives_the_same_solution():
+    from oracle.chi0 import sternheimer_operator
+    from oracle.minres import minres
+    name = "lat2x2_30_1"
+    m = model(name)
+    rng = np.random.default_rng(31)
+    Bm = rng.standard_normal((m.N, 5))
+    shifts = m.eps[rng.integers(0, m.n_orb, 5)]
+    ctx = context(name, stern_tol=1e-12, precision=1, learned=1)
+    ctx.cnn_set_weights(W.learned.init_weights(2, gain=0.5))
+    X1, st1 = ctx.sternheimer_solve(to_gpu(Bm), shifts)
+    X0, st0 = context(name, stern_tol=1e-12, precision=1).sternheimer_solve(to_gpu(Bm), shifts)
+    assert st1["rhs_solved"] == 5 and st0["rhs_solved"] == 5
+    A = sternheimer_operator(m)
+    QB = m.project(Bm)
+    Xo = minres(A, QB, shifts, tol=1e-13)
+    assert rel(to_np(X1), Xo) < 1e-8
+    assert rel(to_np(X1), to_np(X0)) < 1e-8
+
+
+def test_learned_form_argument_errors():
+    import torch
+
+    import paper_1605_08021_gb300 as P
+    name = "lat2x2_32_0"
+    m = model(name)
+    B = torch.zeros((2, m.N), dtype=torch.float64, device="cuda")
+    B[0, 3] = 1.0
+    # learned start without weights: the solve refuses instead of starting from zero
+    ctx = context(name, precision=1, learned=1)
+    with pytest.raises(P.AcpError) as e:
+        ctx.sternheimer_solve(B, m.eps[:2])
+    assert e.value.name == "ACP_E_ARG"
+    with pytest.raises(P.AcpError) as e:
+        ctx.cnn_set_weights(np.zeros(100, dtype=np.float32))
+    assert e.value.name == "ACP_E_ARG"
+    # the network is defined on 2D grids only
+    ctx1 = context("small4_160_0")
+    with pytest.raises(P.AcpError) as e:
+        ctx1.cnn_set_weights(W.learned.init_weights(0))
+    assert e.value.name == "ACP_E_ARG"
