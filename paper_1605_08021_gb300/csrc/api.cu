@@ -604,6 +604,27 @@ acp_status acp_cnn_apply(acp_ctx* ctx, const double* R_d, int ncol, const double
   return ACP_OK;
 }
 
+acp_status acp_cnn_train_step(acp_ctx* ctx, const double* R_d, const double* shift_h, const double* Xstar_d,
+                              int nsamp, float lr, double* loss_h, float* grad_h) {
+  ACP_TRY(check_ctx(ctx));
+  if (!R_d || !shift_h || !Xstar_d || nsamp < 1 || !(lr >= 0.f)) return set_error(ctx, ACP_E_ARG, "bad arguments");
+  double* sh = nullptr;
+  ACP_TRY(ws(ctx, "cnn_tshift", nsamp, &sh));
+  ACP_CUDA(ctx, cudaMemcpyAsync(sh, shift_h, sizeof(double) * nsamp, cudaMemcpyHostToDevice, ctx->stream));
+  return cnn_train_step(ctx, R_d, sh, Xstar_d, nsamp, lr, loss_h, grad_h);
+}
+
+acp_status acp_cnn_get_weights(acp_ctx* ctx, float* w_h) {
+  ACP_TRY(check_ctx(ctx));
+  if (!w_h) return set_error(ctx, ACP_E_ARG, "null pointer");
+  if (!ctx->cnn_ready) return set_error(ctx, ACP_E_ARG, "no network weights (acp_cnn_set_weights)");
+  float* w = nullptr;
+  ACP_TRY(ws(ctx, "cnn_w32", (size_t)ACP_CNN_WEIGHTS, &w));
+  ACP_CUDA(ctx, cudaMemcpyAsync(w_h, w, sizeof(float) * ACP_CNN_WEIGHTS, cudaMemcpyDeviceToHost, ctx->stream));
+  ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return ACP_OK;
+}
+
 acp_status acp_compress(acp_ctx* ctx, const double* G_d, int ncol, int cap, int* n_mu, int* pivots_h, double* Xi_d,
                         double* Rdiag_h) {
   ACP_TRY(check_ctx(ctx));

@@ -15,29 +15,18 @@
 
 #include <mutex>
 
-#include "internal.cuh"
+#include "cnn.cuh"
 
 namespace acp {
 
 namespace {
 
+using namespace cnn;
+
 constexpr int kT = 16;               // output tile edge
 constexpr int kHalo = 4;             // one point per 3 x 3 layer
 constexpr int kIn = kT + 2 * kHalo;  // 24
-constexpr int kC = 32;               // hidden channels
 constexpr int kThreads = 256;
-
-// packed FP32 weights (host layout): W1 (32,2,3,3), b1 (32), W2 (32,32,3,3), b2, W3 (32,32,3,3),
-// b3, W4 (1,32,3,3), b4 (1), each row-major (output channel, input channel, dy + 1, dx + 1)
-constexpr int kW1 = 0, kB1 = kW1 + kC * 2 * 9, kW2 = kB1 + kC, kB2 = kW2 + kC * kC * 9, kW3 = kB2 + kC,
-              kB3 = kW3 + kC * kC * 9, kW4 = kB3 + kC, kB4 = kW4 + kC * 9, kNumWeights = kB4 + 1;
-static_assert(kNumWeights == ACP_CNN_WEIGHTS, "weight count of the header");
-
-// bfloat16 copies on the device: per layer [input channel][tap][output channel] (output channel
-// fastest, so a thread reads the 32 weights of one tap with four 16-byte loads)
-constexpr int kO1 = 0, kO2 = kO1 + 2 * 9 * kC, kO3 = kO2 + kC * 9 * kC, kO4 = kO3 + kC * 9 * kC,
-              kNumBf16 = kO4 + kC * 9;
-constexpr int kNumBias = 3 * kC + 1;
 
 // shared memory: weights, biases, the input tile and two activation tiles
 constexpr size_t kSmWeights = (size_t)kNumBf16 * 2;         // 38592 bytes
@@ -190,19 +179,40 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace
 
-acp_status cnn_set_weights(acp_ctx* ctx, const float* w_h) {
+// bfloat16 copies and FP32 biases from the FP32 master weights in the workspace
+acp_status cnn_repack(acp_ctx* ctx) {
   float* w32 = nullptr;
   __nv_bfloat16* wb = nullptr;
   float* bias = nullptr;
   ACP_TRY(ws(ctx, "cnn_w32", (size_t)kNumWeights, &w32));
   ACP_TRY(ws(ctx, "cnn_bf16", (size_t)kNumBf16, &wb));
   ACP_TRY(ws(ctx, "cnn_bias", (size_t)kNumBias, &bias));
-  ACP_CUDA(ctx, cudaMemcpyAsync(w32, w_h, sizeof(float) * kNumWeights, cudaMemcpyHostToDevice, ctx->stream));
   ::acp::note_launch(ctx);
   cnn_pack_kernel<<<(kNumWeights + 255) / 256, 256, 0, ctx->stream>>>(w32, wb, bias);
   ACP_LAUNCH(ctx);
+  return ACP_OK;
+}
+
+acp_status cnn_col_rms(acp_ctx* ctx, const double* R, int ldr, int ncol, double* rms) {
+  if (ncol <= 0) return ACP_OK;
+  ::acp::note_launch(ctx);
+  col_rms_kernel<<<ncol, 256, 0, ctx->stream>>>(ctx->N, R, ldr, rms);
+  ACP_LAUNCH(ctx);
+  return ACP_OK;
+}
+
+acp_status cnn_set_weights(acp_ctx* ctx, const float* w_h) {
+  float *w32 = nullptr, *m = nullptr, *v = nullptr;
+  ACP_TRY(ws(ctx, "cnn_w32", (size_t)kNumWeights, &w32));
+  ACP_TRY(ws(ctx, "cnn_adam_m", (size_t)kNumWeights, &m));
+  ACP_TRY(ws(ctx, "cnn_adam_v", (size_t)kNumWeights, &v));
+  ACP_CUDA(ctx, cudaMemcpyAsync(w32, w_h, sizeof(float) * kNumWeights, cudaMemcpyHostToDevice, ctx->stream));
+  ACP_CUDA(ctx, cudaMemsetAsync(m, 0, sizeof(float) * kNumWeights, ctx->stream));
+  ACP_CUDA(ctx, cudaMemsetAsync(v, 0, sizeof(float) * kNumWeights, ctx->stream));
+  ACP_TRY(cnn_repack(ctx));
   ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the host buffer may go away
   ctx->cnn_ready = true;
+  ctx->cnn_steps = 0;
   return ACP_OK;
 }
 
@@ -232,9 +242,7 @@ acp_status cnn_initial_guess(acp_ctx* ctx, const double* R, int ldr, int ncol, c
       sm_count[ctx->device] = n > 0 ? n : 1;
     }
   }
-  ::acp::note_launch(ctx);
-  col_rms_kernel<<<ncol, 256, 0, ctx->stream>>>(ctx->N, R, ldr, rms);
-  ACP_LAUNCH(ctx);
+  ACP_TRY(cnn_col_rms(ctx, R, ldr, ncol, rms));
   const long long items = (long long)((ctx->nx + kT - 1) / kT) * ((ctx->ny + kT - 1) / kT) * ncol;
   const int blocks = (int)std::min<long long>(items, sm_count[ctx->device]);
   ::acp::note_launch(ctx);

@@ -85,3 +85,41 @@ def test_learned_form_argument_errors():
     with pytest.raises(P.AcpError) as e:
         ctx1.cnn_set_weights(W.learned.init_weights(0))
     assert e.value.name == "ACP_E_ARG"
+
+
+def test_training_step_matches_oracle():
+    """One training step: the loss and its gradient against the oracle's backward pass (FP64 on
+    the same FP32 master weights; the device runs the forward and data-gradient passes in FP32
+    and sums weight gradients in FP64: 1e-5 on the loss, 1e-4 on the gradient); the Adam update
+    against the oracle's Adam fed the device gradient (FP32 update arithmetic, 1e-6 absolute);
+    the inference copies follow the new weights; and repeated steps lower the loss."""
+    from oracle import cnn as C
+    name = "rect2x2_40x24_0"
+    m = model(name)
+    ctx = context(name)
+    w = W.learned.init_weights(3)
+    ctx.cnn_set_weights(w)
+    rng = np.random.default_rng(32)
+    S = 3
+    R = rng.standard_normal((m.N, S))
+    R[:, 1] = 0.0
+    shifts = m.eps[rng.integers(0, m.n_orb, S)]
+    Xs = rng.standard_normal((m.N, S))
+    loss, g = ctx.cnn_train_step(to_gpu(R), shifts, to_gpu(Xs), lr=1e-3, return_grad=True)
+    params = W.learned.unpack(w)
+    samples = [(R[:, s].reshape(m.ny, m.nx), (m.V - shifts[s]).reshape(m.ny, m.nx), Xs[:, s].reshape(m.ny, m.nx))
+               for s in range(S)]
+    Lo, go = C.loss_and_grads(params, samples)
+    assert abs(loss - Lo) <= 1e-5 * Lo
+    g_ref = np.concatenate([np.concatenate([dW.ravel(), db]) for dW, db in go])
+    assert rel(g.astype(np.float64), g_ref) < 1e-4
+    w1 = ctx.cnn_get_weights()
+    ref = C.Adam(lr=1e-3).step([w.astype(np.float64)], [g.astype(np.float64)])[0]
+    assert np.abs(w1 - ref).max() < 1e-6
+    # the bfloat16 inference copies are rebuilt from the new master weights
+    X0 = to_np(ctx.cnn_apply(to_gpu(R[:, :1]), shifts[:1]))[:, 0]
+    x_ref = C.forward(W.learned.unpack(w1), R[:, 0].reshape(m.ny, m.nx), (m.V - shifts[0]).reshape(m.ny, m.nx),
+                      bf16=True).reshape(-1)
+    assert rel(X0, x_ref) < 2e-5
+    losses = [ctx.cnn_train_step(to_gpu(R), shifts, to_gpu(Xs), lr=1e-3) for _ in range(20)]
+    assert losses[-1] < loss
