@@ -263,17 +263,19 @@ acp_status acp_cnn_set_weights(acp_ctx* ctx, const float* w_h, long long n);
    Errors: ACP_E_ARG (no weights, not a 2D context, bad pointers), ACP_E_CUDA. */
 acp_status acp_cnn_apply(acp_ctx* ctx, const double* R_d, int ncol, const double* shift_h, double* X0_d);
 
-/* One training step of the network on nsamp solved samples (R_j, shift_h[j], X*_j): the loss
-   L = (1/nsamp) sum_j ||x0_j - X*_j||^2 / ||X*_j||^2 with x0_j the network's guess computed with
-   the FP32 master weights, its gradient by the backward pass, and one Adam step (lr; beta1 0.9,
-   beta2 0.999, eps 1e-8, bias-corrected by the number of steps since acp_cnn_set_weights) on
-   the master weights, after which the bfloat16 inference copies are rebuilt.  R_d, Xstar_d:
-   device, N x nsamp; shift_h: host, nsamp values.  loss_h (may be NULL) receives L before the
-   step; grad_h (may be NULL, host, ACP_CNN_WEIGHTS values in the packed order) the gradient.
-   Errors: ACP_E_ARG (no weights, not a 2D context, nsamp outside [1, 65535]), ACP_E_CUDA,
-   ACP_E_OOM. */
-acp_status acp_cnn_train_step(acp_ctx* ctx, const double* R_d, const double* shift_h, const double* Xstar_d,
-                              int nsamp, float lr, double* loss_h, float* grad_h);
+/* One training step of the network on nsamp solved samples on an nx x ny periodic grid (any grid:
+   the context only holds the weights, the Adam state and the stream): sample j is a right-hand
+   side R_j, its shifted potential VS_j = V_eff - s_j of its own system, and the solution X*_j.
+   The loss L = (1/nsamp) sum_j ||x0_j - X*_j||^2 / ||X*_j||^2, with x0_j the network's guess
+   computed with the FP32 master weights; its gradient by the backward pass; one Adam step (lr;
+   beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected by the number of steps since
+   acp_cnn_set_weights) on the master weights; then the bfloat16 inference copies are rebuilt.
+   R_d, VS_d, Xstar_d: device, (nx ny) x nsamp, x fastest.  loss_h (may be NULL) receives L before
+   the step; grad_h (may be NULL, host, ACP_CNN_WEIGHTS values in the packed order) the gradient.
+   Errors: ACP_E_ARG (no weights, nsamp outside [1, 65535], nx or ny below 3, nx ny above 2^26),
+   ACP_E_CUDA, ACP_E_OOM. */
+acp_status acp_cnn_train_step(acp_ctx* ctx, int nx, int ny, const double* R_d, const double* VS_d,
+                              const double* Xstar_d, int nsamp, float lr, double* loss_h, float* grad_h);
 
 /* The FP32 master weights in the packed order (w_h: host, ACP_CNN_WEIGHTS values).
    Errors: ACP_E_ARG (no weights, null pointer), ACP_E_CUDA. */

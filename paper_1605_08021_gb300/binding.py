@@ -106,7 +106,7 @@ def load():
         "acp_compress": (I, [P, P, I, I, POINTER(c_int), POINTER(c_int), P, D]),
         "acp_cnn_set_weights": (I, [P, POINTER(ctypes.c_float), c_longlong]),
         "acp_cnn_apply": (I, [P, P, I, D, P]),
-        "acp_cnn_train_step": (I, [P, P, D, P, I, ctypes.c_float, D, POINTER(ctypes.c_float)]),
+        "acp_cnn_train_step": (I, [P, I, I, P, P, P, I, ctypes.c_float, D, POINTER(ctypes.c_float)]),
         "acp_cnn_get_weights": (I, [P, POINTER(ctypes.c_float)]),
         "acp_update": (I, [P, P, P, D, I]),
         "acp_profile_enable": (I, [P, I]),
@@ -367,20 +367,19 @@ class Context:
         self._call(self.lib.acp_cnn_apply(self.ptr, _tptr(R), R.shape[0], _dptr(sh), _tptr(X0)))
         return X0
 
-    def cnn_train_step(self, R, shifts, Xstar, lr, return_grad=False):
-        """acp_cnn_train_step on the columns of R and Xstar (rows of the tensors); returns the loss
-        before the step (and the gradient if asked)."""
-        _check_block(R, self.N, "R")
-        _check_block(Xstar, self.N, "Xstar")
-        if Xstar.shape != R.shape:
-            raise ValueError("R and Xstar differ in shape")
-        sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
-        if sh.shape != (R.shape[0],):
-            raise ValueError("one shift per sample")
+    def cnn_train_step(self, grid, R, VS, Xstar, lr, return_grad=False):
+        """acp_cnn_train_step on a batch living on grid = (nx, ny): the columns of R, VS (= V - s of
+        each sample) and Xstar are the rows of the tensors.  Returns the loss before the step (and
+        the gradient if asked)."""
+        nx, ny = (int(g) for g in grid)
+        for t, nm in ((R, "R"), (VS, "VS"), (Xstar, "Xstar")):
+            _check_block(t, nx * ny, nm)
+        if not (VS.shape == R.shape == Xstar.shape):
+            raise ValueError("R, VS and Xstar differ in shape")
         loss = np.zeros(1)
         g = np.zeros(ACP_CNN_WEIGHTS, dtype=np.float32) if return_grad else None
         self._call(self.lib.acp_cnn_train_step(
-            self.ptr, _tptr(R), _dptr(sh), _tptr(Xstar), R.shape[0], float(lr), _dptr(loss),
+            self.ptr, nx, ny, _tptr(R), _tptr(VS), _tptr(Xstar), R.shape[0], float(lr), _dptr(loss),
             g.ctypes.data_as(POINTER(ctypes.c_float)) if return_grad else None))
         return (float(loss[0]), g) if return_grad else float(loss[0])
 

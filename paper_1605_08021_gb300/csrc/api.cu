@@ -604,14 +604,11 @@ acp_status acp_cnn_apply(acp_ctx* ctx, const double* R_d, int ncol, const double
   return ACP_OK;
 }
 
-acp_status acp_cnn_train_step(acp_ctx* ctx, const double* R_d, const double* shift_h, const double* Xstar_d,
-                              int nsamp, float lr, double* loss_h, float* grad_h) {
+acp_status acp_cnn_train_step(acp_ctx* ctx, int nx, int ny, const double* R_d, const double* VS_d,
+                              const double* Xstar_d, int nsamp, float lr, double* loss_h, float* grad_h) {
   ACP_TRY(check_ctx(ctx));
-  if (!R_d || !shift_h || !Xstar_d || nsamp < 1 || !(lr >= 0.f)) return set_error(ctx, ACP_E_ARG, "bad arguments");
-  double* sh = nullptr;
-  ACP_TRY(ws(ctx, "cnn_tshift", nsamp, &sh));
-  ACP_CUDA(ctx, cudaMemcpyAsync(sh, shift_h, sizeof(double) * nsamp, cudaMemcpyHostToDevice, ctx->stream));
-  return cnn_train_step(ctx, R_d, sh, Xstar_d, nsamp, lr, loss_h, grad_h);
+  if (!R_d || !VS_d || !Xstar_d || nsamp < 1 || !(lr >= 0.f)) return set_error(ctx, ACP_E_ARG, "bad arguments");
+  return cnn_train_step(ctx, nx, ny, R_d, VS_d, Xstar_d, nsamp, lr, loss_h, grad_h);
 }
 
 acp_status acp_cnn_get_weights(acp_ctx* ctx, float* w_h) {

@@ -193,10 +193,10 @@ acp_status cnn_repack(acp_ctx* ctx) {
   return ACP_OK;
 }
 
-acp_status cnn_col_rms(acp_ctx* ctx, const double* R, int ldr, int ncol, double* rms) {
+acp_status cnn_col_rms(acp_ctx* ctx, int N, const double* R, int ldr, int ncol, double* rms) {
   if (ncol <= 0) return ACP_OK;
   ::acp::note_launch(ctx);
-  col_rms_kernel<<<ncol, 256, 0, ctx->stream>>>(ctx->N, R, ldr, rms);
+  col_rms_kernel<<<ncol, 256, 0, ctx->stream>>>(N, R, ldr, rms);
   ACP_LAUNCH(ctx);
   return ACP_OK;
 }
@@ -242,7 +242,7 @@ acp_status cnn_initial_guess(acp_ctx* ctx, const double* R, int ldr, int ncol, c
       sm_count[ctx->device] = n > 0 ? n : 1;
     }
   }
-  ACP_TRY(cnn_col_rms(ctx, R, ldr, ncol, rms));
+  ACP_TRY(cnn_col_rms(ctx, ctx->N, R, ldr, ncol, rms));
   const long long items = (long long)((ctx->nx + kT - 1) / kT) * ((ctx->ny + kT - 1) / kT) * ncol;
   const int blocks = (int)std::min<long long>(items, sm_count[ctx->device]);
   ::acp::note_launch(ctx);

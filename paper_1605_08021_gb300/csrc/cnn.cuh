@@ -32,8 +32,9 @@ __host__ __device__ constexpr int b_off(int l) { return l == 0 ? kB1 : l == 1 ? 
 
 }  // namespace cnn
 
-// cnn.cu: rebuild the bfloat16 copies from the FP32 master weights; per-column RMS of a block
+// cnn.cu: rebuild the bfloat16 copies from the FP32 master weights; per-column RMS of an N-row
+// block
 acp_status cnn_repack(acp_ctx* ctx);
-acp_status cnn_col_rms(acp_ctx* ctx, const double* R, int ldr, int ncol, double* rms);
+acp_status cnn_col_rms(acp_ctx* ctx, int N, const double* R, int ldr, int ncol, double* rms);
 
 }  // namespace acp

@@ -4,9 +4,10 @@
 // the bfloat16 inference copies are rebuilt.
 //
 // Training computes with the FP32 master weights (inference convolves with their bfloat16
-// roundings).  Activations are stored per layer as [sample][channel][grid point] in FP32; every
-// kernel indexes the periodic 3 x 3 neighbourhood of its grid point directly, so the grids of
-// the training systems need no tiling constraints.
+// roundings).  A batch lives on its own nx x ny grid and carries its shifted potentials V - s per
+// sample, so one context (weights and Adam state) trains on systems of any grid.  Activations
+// are stored per layer as [sample][channel][grid point] in FP32; every kernel indexes the
+// periodic 3 x 3 neighbourhood of its grid point directly (no tiling constraints on the grid).
 //
 // Layer l: z = b + sum_c W[o, c, p+1, q+1] a[c, y+p, x+q] (periodic), a_next = tanh(z) for l < 3.
 //   dL/da[c, y, x] = sum_{o,p,q} W[o, c, p+1, q+1] g[o, y-p, x-q]
@@ -27,15 +28,14 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
-// a0[s] = (R_s / rms_s, V - shift_s) as FP32 (channel 0 is zero for a zero sample)
-__global__ void train_inputs_kernel(int N, int S, const double* __restrict__ R, const double* __restrict__ V,
-                                    const double* __restrict__ shift, const double* __restrict__ rms,
-                                    float* __restrict__ a0) {
+// a0[s] = (R_s / rms_s, VS_s) as FP32 (channel 0 is zero for a zero sample)
+__global__ void train_inputs_kernel(int N, const double* __restrict__ R, const double* __restrict__ VS,
+                                    const double* __restrict__ rms, float* __restrict__ a0) {
   const int s = blockIdx.y;
   const double rs = rms[s];
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
     a0[((size_t)s * 2 + 0) * N + a] = rs > 0.0 ? (float)(R[(size_t)s * N + a] / rs) : 0.f;
-    a0[((size_t)s * 2 + 1) * N + a] = (float)(V[a] - shift[s]);
+    a0[((size_t)s * 2 + 1) * N + a] = (float)VS[(size_t)s * N + a];
   }
 }
 
@@ -174,12 +174,13 @@ __global__ void adam_kernel(int n, float* __restrict__ w, float* __restrict__ m,
 
 }  // namespace
 
-acp_status cnn_train_step(acp_ctx* ctx, const double* R, const double* shift_d, const double* Xs, int S, float lr,
-                          double* loss_h, float* grad_h) {
-  if (ctx->dim != 2) return set_error(ctx, ACP_E_ARG, "the learned initial guess is defined on 2D grids");
+acp_status cnn_train_step(acp_ctx* ctx, int nx, int ny, const double* R, const double* VS, const double* Xs, int S,
+                          float lr, double* loss_h, float* grad_h) {
   if (!ctx->cnn_ready) return set_error(ctx, ACP_E_ARG, "no network weights (acp_cnn_set_weights)");
   if (S < 1 || S > 65535) return set_error(ctx, ACP_E_ARG, "nsamp %d outside [1, 65535]", S);
-  const int N = ctx->N, nx = ctx->nx, ny = ctx->ny;
+  if (nx < 3 || ny < 3 || (long long)nx * ny > (1LL << 26))
+    return set_error(ctx, ACP_E_ARG, "training grid %d x %d outside [3, ...] with nx ny <= 2^26", nx, ny);
+  const int N = nx * ny;
   const size_t hid = (size_t)S * kC * N;
   float *w = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
   float *a0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *z4 = nullptr, *gA = nullptr, *gB = nullptr;
@@ -199,9 +200,9 @@ acp_status cnn_train_step(acp_ctx* ctx, const double* R, const double* shift_d, 
   ACP_TRY(ws(ctx, "cnn_loss", (size_t)S, &loss));
   cudaStream_t st = ctx->stream;
   const dim3 pts((N + kThreads - 1) / kThreads, S);
-  ACP_TRY(cnn_col_rms(ctx, R, N, S, rms));
+  ACP_TRY(cnn_col_rms(ctx, N, R, N, S, rms));
   ::acp::note_launch(ctx);
-  train_inputs_kernel<<<dim3((N + 255) / 256, S), 256, 0, st>>>(N, S, R, ctx->d_V, shift_d, rms, a0);
+  train_inputs_kernel<<<dim3((N + 255) / 256, S), 256, 0, st>>>(N, R, VS, rms, a0);
   ACP_LAUNCH(ctx);
   // forward
   ::acp::note_launch(ctx);

@@ -250,10 +250,11 @@ acp_status project_mixed64(acp_ctx* ctx, const double* X, int ncol, double* Y);
 acp_status cnn_set_weights(acp_ctx* ctx, const float* w_h);
 acp_status cnn_initial_guess(acp_ctx* ctx, const double* R, int ldr, int ncol, const double* shift_d, double* X0,
                              int ldx);
-// cnn_train.cu: one Adam step on nsamp solved samples (R, shift, X*), FP32 master weights; loss
-// before the step to *loss_h; the gradient to grad_h if not null (host, ACP_CNN_WEIGHTS values).
-acp_status cnn_train_step(acp_ctx* ctx, const double* R, const double* shift_d, const double* Xs, int nsamp,
-                          float lr, double* loss_h, float* grad_h);
+// cnn_train.cu: one Adam step on nsamp solved samples (R, V - s, X*) on an nx x ny grid, FP32
+// master weights; loss before the step to *loss_h; the gradient to grad_h if not null (host,
+// ACP_CNN_WEIGHTS values).
+acp_status cnn_train_step(acp_ctx* ctx, int nx, int ny, const double* R, const double* VS, const double* Xs,
+                          int nsamp, float lr, double* loss_h, float* grad_h);
 
 // dense.cu: LU solve of an n x n system with nrhs right-hand sides (A, B overwritten; X in B).
 acp_status lu_solve(acp_ctx* ctx, double* A, int n, double* B, int nrhs);

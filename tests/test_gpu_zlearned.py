@@ -88,11 +88,12 @@ def test_learned_form_argument_errors():
 
 
 def test_training_step_matches_oracle():
-    """One training step: the loss and its gradient against the oracle's backward pass (FP64 on
-    the same FP32 master weights; the device runs the forward and data-gradient passes in FP32
-    and sums weight gradients in FP64: 1e-5 on the loss, 1e-4 on the gradient); the Adam update
-    against the oracle's Adam fed the device gradient (FP32 update arithmetic, 1e-6 absolute);
-    the inference copies follow the new weights; and repeated steps lower the loss."""
+    """One training step on the context's own grid: the loss and its gradient against the
+    oracle's backward pass (FP64 on the same FP32 master weights; the device runs the forward and
+    data-gradient passes in FP32 and sums weight gradients in FP64: 1e-5 on the loss, 1e-4 on the
+    gradient); the Adam update against the oracle's Adam fed the device gradient (FP32 update
+    arithmetic, 1e-6 absolute); the inference copies follow the new weights; and repeated steps
+    lower the loss."""
     from oracle import cnn as C
     name = "rect2x2_40x24_0"
     m = model(name)
@@ -105,7 +106,9 @@ def test_training_step_matches_oracle():
     R[:, 1] = 0.0
     shifts = m.eps[rng.integers(0, m.n_orb, S)]
     Xs = rng.standard_normal((m.N, S))
-    loss, g = ctx.cnn_train_step(to_gpu(R), shifts, to_gpu(Xs), lr=1e-3, return_grad=True)
+    VS = m.V[:, None] - shifts[None, :]
+    grid = (m.nx, m.ny)
+    loss, g = ctx.cnn_train_step(grid, to_gpu(R), to_gpu(VS), to_gpu(Xs), lr=1e-3, return_grad=True)
     params = W.learned.unpack(w)
     samples = [(R[:, s].reshape(m.ny, m.nx), (m.V - shifts[s]).reshape(m.ny, m.nx), Xs[:, s].reshape(m.ny, m.nx))
                for s in range(S)]
@@ -121,5 +124,25 @@ def test_training_step_matches_oracle():
     x_ref = C.forward(W.learned.unpack(w1), R[:, 0].reshape(m.ny, m.nx), (m.V - shifts[0]).reshape(m.ny, m.nx),
                       bf16=True).reshape(-1)
     assert rel(X0, x_ref) < 2e-5
-    losses = [ctx.cnn_train_step(to_gpu(R), shifts, to_gpu(Xs), lr=1e-3) for _ in range(20)]
+    losses = [ctx.cnn_train_step(grid, to_gpu(R), to_gpu(VS), to_gpu(Xs), lr=1e-3) for _ in range(20)]
     assert losses[-1] < loss
+
+
+def test_training_on_another_grid():
+    """A batch on a grid other than the context's (7 x 5 here: every point's neighbourhood wraps)
+    trains the same weights; loss and gradient as in the oracle."""
+    from oracle import cnn as C
+    ctx = context("lat2x2_32_0")
+    w = W.learned.init_weights(4)
+    ctx.cnn_set_weights(w)
+    rng = np.random.default_rng(33)
+    nx, ny, S = 7, 5, 2
+    R = rng.standard_normal((nx * ny, S))
+    VS = rng.standard_normal((nx * ny, S))
+    Xs = rng.standard_normal((nx * ny, S))
+    loss, g = ctx.cnn_train_step((nx, ny), to_gpu(R), to_gpu(VS), to_gpu(Xs), lr=0.0, return_grad=True)
+    samples = [(R[:, s].reshape(ny, nx), VS[:, s].reshape(ny, nx), Xs[:, s].reshape(ny, nx)) for s in range(S)]
+    Lo, go = C.loss_and_grads(W.learned.unpack(w), samples)
+    assert abs(loss - Lo) <= 1e-5 * Lo
+    assert rel(g.astype(np.float64), np.concatenate([np.concatenate([dW.ravel(), db]) for dW, db in go])) < 1e-4
+    assert np.array_equal(ctx.cnn_get_weights(), w)  # lr = 0 leaves the weights as they were
