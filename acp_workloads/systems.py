@@ -202,6 +202,26 @@ def small_lattice(nxa=2, nya=2, n_grid=32, seed=0, spacing=8.0, occ=1, scale=1.0
                       displacement=displacement, rng=rng)
 
 
+def training_lattices(n_sys: int = 200, min_side: int = 3, max_side: int = 5, h: float = 0.5,
+                      first: int = 0) -> list:
+    """Training systems of the learned initial guess: system k has nxa x nya sites (each uniform
+    in [min_side, max_side]) every 10 bohr with uniform +-0.3 displacements and, with probability
+    1/2, one random vacancy; Z = 2, sigma 1.2, kappa 0.01, kernel strength 1, occupation 2 (the
+    closed-shell recipe of configuration 3, which keeps a gap; Z in {1, 2} alloys at occupation 1
+    close it on these lattices), and per axis the smallest 2-3-5-smooth grid with spacing at most
+    h."""
+    out = []
+    for k in range(first, first + n_sys):
+        rng = _rng(5, k)
+        nxa, nya = (int(v) for v in rng.integers(min_side, max_side + 1, 2))
+        vac = (int(rng.integers(0, nxa * nya)),) if rng.random() < 0.5 else ()
+        s = lattice_2d(f"train5_{k}_{nxa}x{nya}", nxa, nya, 10.0, 2.0, 1.2, 0.01, 1.0, 8, 2, vacancies=vac,
+                       displacement=0.3, rng=rng)
+        n = tuple(smooth_5(int(np.ceil(Li / h - 1e-9))) for Li in s.L)
+        out.append(System(**{**s.__dict__, "n": n}))
+    return out
+
+
 def mixed_chain(n_atoms: int, n_grid: int, seed: int = 0, scale: float = 0.5) -> System:
     """Config-2 recipe at another size: atoms every 10 bohr with uniform +-0.5 displacements,
     Z uniform in {1, 2}, sigma 1, kappa 0.01, occupation 1 (for mid-size profiling runs)."""

@@ -74,3 +74,12 @@ def test_grid_support_bounds(lib):
     g.dim = 3
     assert lib.acp_grid_supported(ctypes.byref(g)) == 1
     assert lib.acp_grid_supported(None) == 1
+
+
+def test_training_lattices_have_supported_grids_and_closed_shells():
+    import acp_workloads as W
+    systems = W.training_lattices(208)
+    assert len({s.name for s in systems}) == 208
+    for s in systems:
+        assert P.grid_supported(s.n), s.n
+        assert max(s.h) <= 0.5 + 1e-12 and s.n_elec % 2 == 0 and s.n_orb == s.n_elec // 2
