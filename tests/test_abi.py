@@ -54,6 +54,11 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     out = ctypes.c_void_p()
     assert lib.acp_init(ctypes.byref(out), None, None, None, None, None, 0, None, None) == 1
     assert lib.acp_apply_chi0(None, None, 0, None, None) == 1
+    # the learned initial guess: a null context is refused before any device work
+    assert lib.acp_cnn_set_weights(None, None, 0) == 1
+    assert lib.acp_cnn_apply(None, None, 1, None, None) == 1
+    assert lib.acp_cnn_train_step(None, 8, 8, None, None, None, 1, 0.0, None, None) == 1
+    assert lib.acp_cnn_get_weights(None, None) == 1
 
 
 def _smooth(n):
