@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // the MMAs must be done with the accumulator before it is freed (complete on the normal
     // path, where the epilogue has waited for the same phase)
     if (!tc::mbar_wait(&done_bar, 0, tc::globaltimer_ns() + kWaitNs) && lane == 0) atomicExch(p.status, 1);
+    __syncwarp();  // the dealloc is warp-collective (.sync.aligned): reconverge after the wait
     tc::tmem_dealloc(tmem, p.tmem_cols);
   }
   if (threadIdx.x == 0 && abort_sh) atomicExch(p.status, 1);
