@@ -251,12 +251,12 @@ acp_status cnn_train_step(acp_ctx* ctx, int nx, int ny, const double* R, const d
   ACP_CUDA(ctx, cudaMemcpyAsync(lh.data(), loss, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
   if (grad_h) ACP_CUDA(ctx, cudaMemcpyAsync(grad_h, grad, sizeof(float) * kNumWeights, cudaMemcpyDeviceToHost, st));
   // Adam with the published defaults, bias corrections from the step count
-  const double b1 = 0.9, b2 = 0.999;
+  // (the bias corrections use the same FP32 betas as the moment updates)
+  const float b1 = 0.9f, b2 = 0.999f;
   const long long t = ++ctx->cnn_steps;
-  const float c1 = (float)(1.0 - std::pow(b1, (double)t)), c2 = (float)(1.0 - std::pow(b2, (double)t));
+  const float c1 = (float)(1.0 - std::pow((double)b1, (double)t)), c2 = (float)(1.0 - std::pow((double)b2, (double)t));
   ::acp::note_launch(ctx);
-  adam_kernel<<<(kNumWeights + 255) / 256, 256, 0, st>>>(kNumWeights, w, m, v, grad, lr, (float)b1, (float)b2, 1e-8f,
-                                                          c1, c2);
+  adam_kernel<<<(kNumWeights + 255) / 256, 256, 0, st>>>(kNumWeights, w, m, v, grad, lr, b1, b2, 1e-8f, c1, c2);
   ACP_LAUNCH(ctx);
   ACP_TRY(cnn_repack(ctx));
   ACP_CUDA(ctx, cudaStreamSynchronize(st));
