@@ -154,3 +154,60 @@ def test_dynamical_matrix_equals_frozen_phonon_differences():
             Rm[J, b] -= d
             Dfd[:, 2 * J + b] = -(_forces(Rp) - _forces(Rm)) / (2 * d)
     assert np.linalg.norm(D - Dfd) <= 1e-5 * np.linalg.norm(D)
+
+
+class _FreeGS:
+    pass
+
+
+@pytest.mark.parametrize("occ", [1, 2])
+def test_free_electron_lindhard_2d(occ):
+    """V_eff = 0 in a rectangular box with the five lowest planewaves occupied (k = 0, +-k_x1,
+    +-k_y1): Alg. 1 acting on e^{iq.r} gives chihat(q) e^{iq.r} with the 2D Lindhard sum
+    chihat(q) = (f/A) sum_{k occ} sum_{+-} 1(k +- q unocc) / (eps_k - eps_{k+-q}),
+    the free-electron response written out in planewaves (A = Lx Ly)."""
+    from oracle import chi0 as C
+    nx, ny, Lx, Ly = 24, 20, 12.0, 10.0
+    s = W.lattice_2d("free2d", 1, 1, 1.0, 1.0, 0.5, 0.1, 1.0, 8, 1)
+    s = W.System(**{**s.__dict__, "n": (nx, ny), "L": (Lx, Ly)})
+    A = Lx * Ly
+    ys, xs = np.meshgrid(np.arange(ny) * Ly / ny, np.arange(nx) * Lx / nx, indexing="ij")
+    xs, ys = xs.reshape(-1), ys.reshape(-1)   # index ix + nx iy
+    occn = [(0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)]
+
+    def kvec(n):
+        return 2 * np.pi * n[0] / Lx, 2 * np.pi * n[1] / Ly
+
+    def energy(n):
+        kx, ky = kvec(n)
+        return 0.5 * (kx * kx + ky * ky)
+
+    cols, eps = [np.full(nx * ny, 1 / np.sqrt(A))], [0.0]
+    for n in [(1, 0), (0, 1)]:
+        kx, ky = kvec(n)
+        ph = kx * xs + ky * ys
+        cols += [np.sqrt(2 / A) * np.cos(ph), np.sqrt(2 / A) * np.sin(ph)]
+        eps += [energy(n)] * 2
+    order = np.argsort(eps, kind="stable")
+    gs = _FreeGS()
+    gs.V = np.zeros(nx * ny)
+    gs.psi = np.array(cols).T[:, order]
+    gs.eps = np.array(eps)[order]
+    gs.n_orb = len(eps)
+    gs.rho = occ * np.sum(gs.psi ** 2, axis=1)
+    m = Model2D(s, gs)
+    m.f = occ
+    assert np.allclose(gs.psi.T @ gs.psi * m.h, np.eye(5), atol=1e-12)
+    occset = set(occn)
+    for q in [(1, 0), (1, 1), (2, -1), (0, 3)]:
+        chi = 0.0
+        for n in occn:
+            for sgn in (1, -1):
+                nq = (n[0] + sgn * q[0], n[1] + sgn * q[1])
+                if nq not in occset:
+                    chi += 1.0 / (energy(n) - energy(nq))
+        chi *= occ / A
+        qx, qy = kvec(q)
+        g = np.stack([np.cos(qx * xs + qy * ys), np.sin(qx * xs + qy * ys)], axis=1)
+        U = C.chi0_apply(m, g)
+        assert np.allclose(U, chi * g, atol=1e-10 * abs(chi)), q
