@@ -376,10 +376,19 @@ def compare_forms(P, s, gs, om, V, psi, rho, R, Z, sig):
 
 
 def accuracy(D, w):
-    """Errors against the exact dynamical matrix of the 128-atom chain written by the oracle
-    (tests/golden/c2_exact_dmat.npz): relative Frobenius error of D and max |omega - omega_ref| /
-    max |omega_ref|.  None for other workloads."""
+    """Errors against exact references written by the oracle: for the 128-atom chain
+    (tests/golden/c2_exact_dmat.npz) the relative Frobenius error of D and max |omega -
+    omega_ref| / max |omega_ref|; for the 2D lattice (tests/golden/c3_exact_dcols.npz, a sample of
+    exact columns of D) the relative Frobenius error of those columns.  None otherwise."""
     import numpy as np
+    if WORKLOAD == "c3":
+        path = os.path.join(ROOT, "tests", "golden", "c3_exact_dcols.npz")
+        if not os.path.exists(path):
+            return None
+        ref = np.load(path)
+        cols = ref["cols"]
+        return {"D_cols_rel_fro": float(np.linalg.norm(D[:, cols] - ref["D_cols"]) / np.linalg.norm(ref["D_cols"])),
+                "sampled_columns": [int(c) for c in cols]}
     path = os.path.join(ROOT, "tests", "golden", "c2_exact_dmat.npz")
     if WORKLOAD != "c2" or not os.path.exists(path):
         return None
