@@ -107,9 +107,12 @@ def build_W(model, zetas, nodes, pivots):
     return W
 
 
-def compressed_chi0(model, Gk, Omega, eps_tol, n_cheb, tol=1e-12):
-    """Alg. 3: returns (W, pivots, compression) with chi0_tilde = W Pi^T."""
-    comp = interpolative_decomposition(model, Gk, Omega, eps_tol)
+def compressed_chi0(model, Gk, Omega, eps_tol, n_cheb, tol=1e-12, max_rank=None):
+    """Alg. 3: returns (W, pivots, compression) with chi0_tilde = W Pi^T.
+
+    ``max_rank`` caps N_mu; with ``eps_tol = 0`` it fixes N_mu, as Table 1 does (N_mu = l N_e).
+    """
+    comp = interpolative_decomposition(model, Gk, Omega, eps_tol, max_rank=max_rank)
     nodes = chebyshev_nodes(model.eps[0], model.eps[-1], n_cheb)
     zetas = compressed_solves(model, comp.Xi, nodes, tol=tol)
     W = build_W(model, zetas, nodes, comp.pivots)
@@ -122,15 +125,17 @@ def chi0_acp_apply(model, G, Omega, eps_tol, n_cheb, tol=1e-12):
     return W @ np.asarray(G)[piv, :]
 
 
-def chi_acp(model, G, Omega, eps_tol, n_cheb, delta=1e-9, maxit=8, tol=1e-12, history=None):
-    """Alg. 4: U ~ chi G with the adaptively compressed polarizability."""
+def chi_acp(model, G, Omega, eps_tol, n_cheb, delta=1e-9, maxit=8, tol=1e-12, history=None,
+            max_rank=None):
+    """Alg. 4: U ~ chi G with the adaptively compressed polarizability (``max_rank`` as in
+    ``compressed_chi0``)."""
     G = np.asarray(G, dtype=np.float64)
     B = model.apply_Kinv(G)
     Ut = B.copy()
     iters = 0
     for k in range(maxit):
         Gk = model.apply_K(Ut)
-        W, piv, _ = compressed_chi0(model, Gk, Omega, eps_tol, n_cheb, tol=tol)
+        W, piv, _ = compressed_chi0(model, Gk, Omega, eps_tol, n_cheb, tol=tol, max_rank=max_rank)
         S = model.apply_K(W)[piv, :]
         X = np.linalg.solve(np.eye(piv.size) - S, G[piv, :])
         Ut_new = B + W @ X
