@@ -412,11 +412,11 @@ class Context:
 
 
 def grid_supported(n):
-    """acp_grid_supported: whether a context accepts a grid of n points (an int, 1D) or n = (nx, ny)
-    (2D).  Host only."""
+    """acp_grid_supported: whether a context accepts a grid of n points (an int or a 1-tuple, 1D) or
+    n = (nx, ny) (2D).  Host only."""
     g = Grid()
-    if np.ndim(n) == 0:
-        g.dim, g.n[0], g.n[1] = 1, int(n), 1
+    if np.ndim(n) == 0 or len(n) == 1:
+        g.dim, g.n[0], g.n[1] = 1, int(np.ravel(n)[0]), 1
     else:
         g.dim, g.n[0], g.n[1] = 2, int(n[0]), int(n[1])
     return load().acp_grid_supported(ctypes.byref(g)) == 0

@@ -88,3 +88,32 @@ def test_training_lattices_have_supported_grids_and_closed_shells():
     for s in systems:
         assert P.grid_supported(s.n), s.n
         assert max(s.h) <= 0.5 + 1e-12 and s.n_elec % 2 == 0 and s.n_orb == s.n_elec // 2
+
+
+def test_benchmark_recipes_match_their_statements(lib):
+    """The seeded inputs of configurations 1-4 have the sizes, charges, displacements and
+    kernel strengths their recipes state, and every grid is one the library accepts."""
+    import numpy as np
+
+    import acp_workloads as W
+    c1 = W.config(1)
+    assert c1.n == (320,) and c1.L == (80.0,) and c1.occ == 2 and np.all(c1.Z == 2.0)
+    assert np.allclose(np.diff(c1.R[:, 0]), 10.0) and c1.n_orb == 8
+    c2 = W.config(2)
+    site = (np.arange(128) + 0.5) * 10.0
+    assert c2.n == (5120,) and c2.occ == 1 and c2.scale == 0.5 and set(np.unique(c2.Z)) == {1.0, 2.0}
+    assert np.abs(c2.R[:, 0] - site).max() <= 0.5 and c2.n_orb == int(c2.Z.sum())
+    c3 = W.config(3)
+    assert c3.n == (160, 160) and c3.R.shape == (63, 2) and c3.occ == 2 and c3.n_orb == 63
+    c4 = W.batch_config(4)
+    assert len(c4) == 64 and len({s.name for s in c4}) == 64
+    for s in c4:
+        na = s.R.shape[0]
+        assert 16 <= na <= 256 and 0.3 <= s.scale <= 1.0 and s.occ == 1
+        assert s.n[0] == W.systems.smooth_5(40 * na) and s.n[0] >= 40 * na
+        assert 0.23 < s.h[0] <= 0.25 + 1e-12 and P.grid_supported(s.n), s.name
+        assert np.abs(s.R[:, 0] - (np.arange(na) + 0.5) * 10.0).max() <= 0.5
+    # seeded: the same recipe gives the same systems
+    assert all(np.array_equal(a.R, b.R) and np.array_equal(a.Z, b.Z) for a, b in zip(c4, W.batch_config(4)))
+    for P_ in (c1, c2, c3):
+        assert P.grid_supported(P_.n)
