@@ -210,6 +210,16 @@ acp_status acp_batch_dynamical_matrix(acp_ctx* const* ctxs, int n_sys, const acp
    n <= 1024. */
 acp_status acp_phonons(acp_ctx* ctx, const double* D_h, int n, double* omega_h, double* modes_h);
 
+/* Phonon spectrum, the density of states of D (Eq. phononspec, Sec. 2.2), with the Dirac delta
+   replaced by the Gaussian of Sec. 4.1, delta_sigma(x) = exp(-x^2 / 2 sigma^2) / sqrt(2 pi sigma^2):
+   rho_h[j] = (1 / n) sum_k delta_sigma(w_h[j] - omega_h[k]) for the n = d N_A frequencies omega_h
+   (as acp_phonons returns them) at the n_w sample points w_h.  All pointers are host memory owned
+   by the caller; rho_h (n_w entries) is written only on ACP_OK.  ACP_E_ARG for n < 1, n_w < 0,
+   sigma not positive and finite, a NULL pointer (w_h and rho_h may be NULL when n_w = 0) or a
+   non-finite frequency or sample point.  Host only (n * n_w exponentials): callable without a
+   GPU and without a context. */
+acp_status acp_phonon_dos(const double* omega_h, int n, const double* w_h, int n_w, double sigma, double* rho_h);
+
 /* ---- stage-level entry points (used by the parity tests) ------------------------------- */
 
 /* Y = (H - diag(shift)) X, i.e. column j is -1/2 X_j'' + V_eff X_j - shift_h[j] X_j

@@ -5,7 +5,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 Eq. SecDeriv: d^2E/dR_I dR_J = int g_I (chi g_J) + delta_IJ int rho d^2V_I/dR_I^2 + d^2E_II/dR_I dR_J,
 with chi g_J = U_J from the Dyson equation (Eq. chiterm).  D_IJ = that / sqrt(M_I M_J) and
 D u_k = omega_k^2 u_k (Sec. 2.2).  Frequencies of negative eigenvalues are reported as
--sqrt(|lambda|).
+-sqrt(|lambda|).  Eq. phononspec: the phonon spectrum rho_D(w) = (1 / d N_A) sum_k delta(w - omega_k),
+with the Gaussian regularised delta of Sec. 4.1.
 """
 from __future__ import annotations
 
@@ -36,3 +37,14 @@ def dynamical_matrix(model, U, symmetrize=True):
 def phonons(D):
     lam, modes = np.linalg.eigh(0.5 * (D + D.T))
     return np.sign(lam) * np.sqrt(np.abs(lam)), modes
+
+
+def phonon_dos(omega, w, sigma):
+    """Eq. phononspec with delta_sigma(x) = exp(-x^2 / (2 sigma^2)) / sqrt(2 pi sigma^2) (Sec. 4.1):
+    rho(w_j) = (1 / n) sum_k delta_sigma(w_j - omega_k), n = d N_A = len(omega)."""
+    omega = np.asarray(omega, dtype=np.float64)
+    w = np.atleast_1d(np.asarray(w, dtype=np.float64))
+    rho = np.zeros(w.size)
+    for wk in omega:
+        rho += np.exp(-((w - wk) ** 2) / (2.0 * sigma ** 2)) / np.sqrt(2.0 * np.pi * sigma ** 2)
+    return rho / omega.size

@@ -95,6 +95,7 @@ def load():
         "acp_perturbations": (I, [P, POINTER(Atoms), P, P, P]),
         "acp_dynamical_matrix": (I, [P, POINTER(Atoms), P, D, P, POINTER(Stats)]),
         "acp_phonons": (I, [P, D, I, D, D]),
+        "acp_phonon_dos": (I, [D, I, D, I, ctypes.c_double, D]),
         "acp_batch_dynamical_matrix": (I, [POINTER(P), I, POINTER(Atoms), POINTER(P), POINTER(D), POINTER(Stats),
                                            POINTER(c_int), I]),
         "acp_hamiltonian_apply": (I, [P, P, I, D, P]),
@@ -420,6 +421,18 @@ def grid_supported(n):
     else:
         g.dim, g.n[0], g.n[1] = 2, int(n[0]), int(n[1])
     return load().acp_grid_supported(ctypes.byref(g)) == 0
+
+
+def phonon_dos(omega, w, sigma):
+    """acp_phonon_dos: the phonon spectrum of the frequencies omega at the points w with Gaussian
+    width sigma.  Host only."""
+    om = np.ascontiguousarray(omega, dtype=np.float64).ravel()
+    ws_ = np.ascontiguousarray(w, dtype=np.float64).ravel()
+    rho = np.empty_like(ws_)
+    st = load().acp_phonon_dos(_dptr(om), om.size, _dptr(ws_), ws_.size, float(sigma), _dptr(rho))
+    if st != 0:
+        raise AcpError(st, "acp_phonon_dos: n >= 1, sigma > 0 and finite inputs are required")
+    return rho
 
 
 def batch_dynamical_matrix(contexts, atoms, rhos, n_workers=0):

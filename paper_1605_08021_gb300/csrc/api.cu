@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <thread>
@@ -207,6 +208,29 @@ acp_status acp_grid_supported(const acp_grid* g) {
   if (g->dim == 1) return acp::make_fft_plan(g->n[0], &p) ? ACP_OK : ACP_E_ARG;
   if (g->dim == 2) return (acp::make_axis_plan(g->n[0], &p) && acp::make_axis_plan(g->n[1], &p)) ? ACP_OK : ACP_E_ARG;
   return ACP_E_ARG;
+}
+
+acp_status acp_phonon_dos(const double* omega_h, int n, const double* w_h, int n_w, double sigma, double* rho_h) {
+  if (!omega_h || n < 1 || n_w < 0 || !(sigma > 0.0) || !std::isfinite(sigma)) return ACP_E_ARG;
+  if (n_w == 0) return ACP_OK;
+  if (!w_h || !rho_h) return ACP_E_ARG;
+  for (int k = 0; k < n; ++k)
+    if (!std::isfinite(omega_h[k])) return ACP_E_ARG;
+  for (int j = 0; j < n_w; ++j)
+    if (!std::isfinite(w_h[j])) return ACP_E_ARG;
+  // delta_sigma(x) = exp(-x^2 / (2 sigma^2)) / sqrt(2 pi sigma^2); the 1 / n of the spectrum is
+  // folded into the prefactor
+  const double inv2s2 = 0.5 / (sigma * sigma);
+  const double pref = 1.0 / (std::sqrt(2.0 * M_PI * sigma * sigma) * n);
+  for (int j = 0; j < n_w; ++j) {
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const double x = w_h[j] - omega_h[k];
+      acc += std::exp(-x * x * inv2s2);
+    }
+    rho_h[j] = pref * acc;
+  }
+  return ACP_OK;
 }
 
 acp_status acp_init(acp_ctx** out, const acp_grid* g, const acp_kernel* k, const double* v_eff_d,

@@ -82,3 +82,32 @@ def test_dynamical_matrix_equals_frozen_phonon_differences():
             cols.append(-(Fp - Fm) / (2 * d))
         Dfd[:, J] = (4 * cols[1] - cols[0]) / 3.0
     assert np.linalg.norm(D - Dfd) <= 1e-6 * np.linalg.norm(D)
+
+
+def test_phonon_dos_normalisation_moments_and_counting():
+    """Eq. phononspec with the Gaussian delta of Sec. 4.1: rho_D integrates to 1 (the 1 / d N_A
+    normalisation), its mean is the mean frequency and its variance the frequencies' variance plus
+    sigma^2; each mode is scipy's normal density; as sigma -> 0 the integral of rho_D up to a point
+    between two frequencies counts the fraction of modes below it."""
+    from scipy import integrate, stats
+    rng = np.random.default_rng(7)
+    om = np.sort(np.concatenate([[0.0, 0.0], rng.uniform(0.05, 0.9, 14)]))
+    sig = 0.01
+    lo, hi = om.min() - 40 * sig, om.max() + 40 * sig
+    pts = list(om)
+    f = lambda x: Dm.phonon_dos(om, x, sig)[0]  # noqa: E731
+    mass = integrate.quad(f, lo, hi, points=pts, limit=500)[0]
+    mean = integrate.quad(lambda x: x * f(x), lo, hi, points=pts, limit=500)[0]
+    var = integrate.quad(lambda x: (x - mean) ** 2 * f(x), lo, hi, points=pts, limit=500)[0]
+    assert abs(mass - 1.0) < 1e-9
+    assert abs(mean - om.mean()) < 1e-9
+    assert abs(var - (om.var() + sig ** 2)) < 1e-9
+    w = np.linspace(-0.1, 1.0, 301)
+    ref = stats.norm.pdf(w[:, None], loc=om[None, :], scale=sig).mean(axis=1)
+    assert np.allclose(Dm.phonon_dos(om, w, sig), ref, rtol=1e-13, atol=1e-300)
+    gaps = np.diff(om)
+    j = int(np.argmax(gaps))
+    cut = 0.5 * (om[j] + om[j + 1])
+    xs = np.arange(-0.05, cut, 1e-5)  # sigma / 10: the trapezoid rule is exact to rounding here
+    below = np.trapezoid(Dm.phonon_dos(om, xs, 1e-4), xs)
+    assert abs(below - (j + 1) / om.size) < 1e-9
