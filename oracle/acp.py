@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
 Steps, in the paper's order and notation:
-  Alg. 2 with the Remark: the SRFT is applied to G only, G_tilde = G Omega (Omega drawn by
+  Alg. 2 (step 1 as written, or with the Remark): the SRFT of M, or of G only, G_tilde = G Omega (Omega drawn by
     ``acp_workloads.srft_sketch``; complex columns are split into real and imaginary parts).
     Row alpha of M_tilde is the Kronecker product psi(r_alpha, :) (x) G_tilde(r_alpha, :), with
     the stacked column index i + t * N_e (Sec. 2.2).  Pivoted QR of M_tilde^T (LAPACK geqp3),
@@ -66,9 +66,19 @@ def sketch_rows(model, Gk, Omega):
     return np.transpose(M, (0, 2, 1)).reshape(N, -1).T    # rows ordered i + t N_e
 
 
-def interpolative_decomposition(model, Gk, Omega, eps_tol, max_rank=None):
-    """Alg. 2 steps 2-4 on the sketched matrix of the Remark."""
-    MT = sketch_rows(model, Gk, Omega)
+def full_sketch_rows(model, Gk, Omega):
+    """Alg. 2 step 1 as written (no Remark): M_tilde = M Omega, where column I = i + N_e j of M is
+    psi_i * g_j (Eq. MID) and Omega ((N_e N_p) x n_s) holds the real and imaginary parts of the SRFT
+    columns over the index I.  Returns M_tilde^T (n_s x N_g)."""
+    Gk = np.asarray(Gk, dtype=np.float64)
+    M = (model.psi[:, None, :] * Gk[:, :, None]).reshape(model.N, -1)  # (N, N_p, N_e): I = i + N_e j
+    return (M @ np.asarray(Omega, dtype=np.float64)).T
+
+
+def interpolative_decomposition(model, Gk, Omega, eps_tol, max_rank=None, full=False):
+    """Alg. 2 steps 2-4 on the sketched matrix: the Remark's (Omega over the N_p columns of G), or
+    with ``full`` step 1 as written (Omega over the N_e N_p columns of M)."""
+    MT = full_sketch_rows(model, Gk, Omega) if full else sketch_rows(model, Gk, Omega)
     R, piv = sla.qr(MT, mode="r", pivoting=True)
     d = np.abs(np.diag(R))
     n_mu = int(np.sum(d >= eps_tol * d[0]))

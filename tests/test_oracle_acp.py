@@ -133,3 +133,25 @@ def test_table1_capped_rank_cell():
     err = np.linalg.norm(U - Ud) / np.linalg.norm(Ud)
     paper = golden["rows"]["5"][0]
     assert abs(err / paper - 1.0) < 0.25, err
+
+
+def test_full_srft_of_M(small):
+    """Alg. 2 step 1 as written sketches the N_e N_p columns of M itself.  Its sketch with
+    Omega = Omega_G (x) I_{N_e} is exactly the Remark's sketch with Omega_G (the Remark's row
+    psi(r, :) (x) G_tilde(r, :) is that Kronecker product), so both select the same points; and a
+    genuine SRFT over M's columns gives an ID of M within the threshold with Xi(r_mu, :) = I."""
+    s, gs, m, Cm, G = small
+    Om = W.srft_sketch(G.shape[1], 8, 0)
+    kron = np.kron(Om, np.eye(m.n_orb))
+    a, b = A.full_sketch_rows(m, G, kron), A.sketch_rows(m, G, Om)
+    assert np.abs(a - b).max() <= 1e-14 * np.abs(b).max()
+    c_full = A.interpolative_decomposition(m, G, kron, 1e-6, full=True)
+    c_rem = A.interpolative_decomposition(m, G, Om, 1e-6)
+    assert np.array_equal(c_full.pivots, c_rem.pivots)
+    M = (m.psi[:, :, None] * G[:, None, :]).reshape(m.N, -1)
+    Om_full = W.srft_sketch(M.shape[1], 8 * m.n_orb, 1)
+    for eps in (1e-3, 1e-6):
+        comp = A.interpolative_decomposition(m, G, Om_full, eps, full=True)
+        assert np.allclose(comp.Xi[comp.pivots, :], np.eye(comp.pivots.size), atol=1e-12)
+        Mrec = comp.Xi @ M[comp.pivots, :]
+        assert np.linalg.norm(M - Mrec) <= 100 * eps * np.linalg.norm(M)
