@@ -90,8 +90,18 @@ def interpolative_decomposition(model, Gk, Omega, eps_tol, max_rank=None, full=F
     return Compression(pivots=piv[:n_mu].copy(), Xi=XiT.T.copy(), Rdiag=d)
 
 
-def compressed_solves(model, Xi, nodes, tol=1e-12, maxit=5000, chunk=2048):
-    """Eq. eqncompressU: zeta[c][:, mu] solves Q(eps_c - H)Q zeta = Q xi_mu."""
+def compressed_solves(model, Xi, nodes, tol=1e-12, maxit=5000, chunk=2048, spectrum=None):
+    """Eq. eqncompressU: zeta[c][:, mu] solves Q(eps_c - H)Q zeta = Q xi_mu.
+
+    By MINRES, or, when ``spectrum`` = (w, Phi) holds every eigenpair of the grid Hamiltonian
+    (``chi0.full_spectrum``, small grids), exactly in that eigenbasis: on range(Q), spanned by the
+    unoccupied eigenvectors phi_a, zeta = sum_{a > N_e} phi_a (phi_a . xi_mu h) / (eps_c - eps_a).
+    """
+    if spectrum is not None:
+        w, Phi = spectrum
+        Pu, wu = Phi[:, model.n_orb:], w[model.n_orb:]
+        T = (Pu.T @ np.asarray(Xi, dtype=np.float64)) * model.h     # (N_u, N_mu)
+        return [Pu @ (T / (ec - wu)[:, None]) for ec in nodes]
     A = sternheimer_operator(model)
     RHS = model.project(Xi)
     n_mu = Xi.shape[1]
@@ -117,14 +127,15 @@ def build_W(model, zetas, nodes, pivots):
     return W
 
 
-def compressed_chi0(model, Gk, Omega, eps_tol, n_cheb, tol=1e-12, max_rank=None):
+def compressed_chi0(model, Gk, Omega, eps_tol, n_cheb, tol=1e-12, max_rank=None, spectrum=None):
     """Alg. 3: returns (W, pivots, compression) with chi0_tilde = W Pi^T.
 
     ``max_rank`` caps N_mu; with ``eps_tol = 0`` it fixes N_mu, as Table 1 does (N_mu = l N_e).
+    ``spectrum`` selects the exact eigenbasis solves of ``compressed_solves``.
     """
     comp = interpolative_decomposition(model, Gk, Omega, eps_tol, max_rank=max_rank)
     nodes = chebyshev_nodes(model.eps[0], model.eps[-1], n_cheb)
-    zetas = compressed_solves(model, comp.Xi, nodes, tol=tol)
+    zetas = compressed_solves(model, comp.Xi, nodes, tol=tol, spectrum=spectrum)
     W = build_W(model, zetas, nodes, comp.pivots)
     return W, comp.pivots, comp
 
@@ -136,16 +147,17 @@ def chi0_acp_apply(model, G, Omega, eps_tol, n_cheb, tol=1e-12):
 
 
 def chi_acp(model, G, Omega, eps_tol, n_cheb, delta=1e-9, maxit=8, tol=1e-12, history=None,
-            max_rank=None):
-    """Alg. 4: U ~ chi G with the adaptively compressed polarizability (``max_rank`` as in
-    ``compressed_chi0``)."""
+            max_rank=None, spectrum=None):
+    """Alg. 4: U ~ chi G with the adaptively compressed polarizability (``max_rank`` and
+    ``spectrum`` as in ``compressed_chi0``)."""
     G = np.asarray(G, dtype=np.float64)
     B = model.apply_Kinv(G)
     Ut = B.copy()
     iters = 0
     for k in range(maxit):
         Gk = model.apply_K(Ut)
-        W, piv, _ = compressed_chi0(model, Gk, Omega, eps_tol, n_cheb, tol=tol, max_rank=max_rank)
+        W, piv, _ = compressed_chi0(model, Gk, Omega, eps_tol, n_cheb, tol=tol, max_rank=max_rank,
+                                    spectrum=spectrum)
         S = model.apply_K(W)[piv, :]
         X = np.linalg.solve(np.eye(piv.size) - S, G[piv, :])
         Ut_new = B + W @ X
