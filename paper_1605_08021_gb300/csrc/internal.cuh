@@ -206,6 +206,9 @@ struct SolveReport {
 // Solve Q(H - shift_d[j])Q X_j = B_j (B must already be projected) for ncol columns.
 acp_status minres_batched(acp_ctx* ctx, const double* B, int ncol, const double* shift_d, double* X,
                           SolveReport* rep, double t0_ms);
+// The FP64 batched solve whatever opt.precision says, to relative residual tol (X starts at 0).
+acp_status minres_batched_fp64(acp_ctx* ctx, const double* B, int ncol, const double* shift_d, double* X,
+                               double tol, SolveReport* rep, double t0_ms);
 // Multi-shift: for each column mu of B solve Q(H - nodes[c])Q X_{c,mu} = B_mu for all c.
 // X layout: column mu + c * ncol of an N x (nc * ncol) block.
 acp_status minres_multishift(acp_ctx* ctx, const double* B, int ncol, const double* nodes_d, int nc, double* X,

@@ -497,6 +497,12 @@ acp_status minres_batched(acp_ctx* ctx, const double* B, int ncol, const double*
                           SolveReport* rep, double t0_ms) {
   if (ncol <= 0) return ACP_OK;
   if (ctx->opt.precision == ACP_PREC_MIXED) return minres_batched_mixed(ctx, B, ncol, shift_d, X, rep, t0_ms);
+  return minres_batched_fp64(ctx, B, ncol, shift_d, X, ctx->opt.stern_tol, rep, t0_ms);
+}
+
+acp_status minres_batched_fp64(acp_ctx* ctx, const double* B, int ncol, const double* shift_d, double* X,
+                               double tol, SolveReport* rep, double t0_ms) {
+  if (ncol <= 0) return ACP_OK;
   const int N = ctx->N;
   const size_t nv = (size_t)N * ncol;
   MinresState s{};
@@ -514,7 +520,6 @@ acp_status minres_batched(acp_ctx* ctx, const double* B, int ncol, const double*
   ::acp::note_launch(ctx);
   minres_init_kernel<<<ncol, kThreads, 0, ctx->stream>>>(N, B, s, X, ctx->d_flag);
   ACP_LAUNCH(ctx);
-  const double tol = ctx->opt.stern_tol;
   const int maxit = ctx->opt.stern_maxit;
   const int period = projection_period(ctx);
   for (int it = 0; it < maxit; ++it) {

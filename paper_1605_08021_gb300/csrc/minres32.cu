@@ -14,6 +14,8 @@
 // FP32 blocks use the leading dimension ctx->ld32 (N rounded up to 32; the padding is zero).
 #include "internal.cuh"
 
+#include <vector>
+
 namespace acp {
 
 int projection_period(const acp_ctx* ctx);
@@ -178,32 +180,80 @@ __global__ void __launch_bounds__(kThreads) scale_to_f32_kernel(int N, int ld32,
   }
 }
 
-// After the FP32 projection of R32: the projected residual norm is ||R32_j|| * scale_j.  Columns at
-// or below tol (relative to ||B_j||) are converged: masked, and their R32 zeroed.
+// After the FP32 projection of R32: the projected residual norm is ||R32_j|| * scale_j, relative
+// rel_j = that / ||B_j||.  The FP64 residual B - (H - s)X cannot be evaluated more accurately than
+// the rounding of its own evaluation: the FFT of the kinetic term errs by ~log2(N) u ||x|| times the
+// largest multiplier (the standard forward-error bound of the radix FFT), so
+//   floor_j = (log2 N + 4) u (||H||_bound + |s_j|) ||X_j|| / ||B_j||,  u = 2^-53,
+// with ||H||_bound = max k^2/2 + max |V| (hbound).  Column j is converged when rel_j <= max(tol,
+// floor_j): masked, and its R32 zeroed.  From the third round on, a column whose round gained less
+// than 10x has met the attainable accuracy of its FP32 inner solves (shifts close to an eigenvalue
+// make Q(H - s)Q ill conditioned, and FP32 Lanczos then stalls at its own floor): it leaves the FP32
+// rounds and is finished by FP64 MINRES (polish_fp64 below).
 // The inner solve of column j only has to reduce its residual by the factor tol / rel_j that is
 // still missing (with a margin of 4, never below the FP32 floor kInnerTol, never above 1e-2).
 __global__ void __launch_bounds__(kThreads) refine_check_kernel(int N, int ld32, float* __restrict__ R32,
+                                                                const double* __restrict__ X,
+                                                                const double* __restrict__ shift,
+                                                                const double* __restrict__ hbound, double log_fac,
                                                                 const double* __restrict__ scale,
                                                                 const double* __restrict__ bnorm, double tol,
-                                                                double* __restrict__ rel, int* __restrict__ act,
+                                                                double* __restrict__ rel, double* __restrict__ prev,
+                                                                double* __restrict__ floor_out, int round,
+                                                                int* __restrict__ act,
                                                                 double* __restrict__ tol_in, double floor_tol) {
   __shared__ float red[32];
+  __shared__ double red64[32];
   const int j = blockIdx.x;
   float* o = R32 + (size_t)j * ld32;
+  const double* x = X + (size_t)j * N;
   float acc = 0.f;
-  for (int a = threadIdx.x; a < N; a += blockDim.x) acc = fmaf(o[a], o[a], acc);
+  double xacc = 0.0;
+  for (int a = threadIdx.x; a < N; a += blockDim.x) {
+    acc = fmaf(o[a], o[a], acc);
+    xacc += x[a] * x[a];
+  }
   const double pn = sqrt((double)block_sum32(acc, red));
+  const double xn = sqrt(block_sum(xacc, red64));
   const double bn = bnorm[j];
   const double rl = (bn > 0.0) ? pn * scale[j] / bn : 0.0;
-  const bool go = rl > tol;
+  const double fl = (bn > 0.0) ? log_fac * 0x1p-53 * (hbound[0] + fabs(shift[j])) * xn / bn : 0.0;
+  const double lim = fmax(tol, fl);
+  const bool stalled = round > 1 && rl > 0.1 * prev[j];
+  const bool go = rl > lim && !stalled;
   if (!go)
     for (int a = threadIdx.x; a < N; a += blockDim.x) o[a] = 0.f;
   if (threadIdx.x == 0) {
     rel[j] = rl;
+    prev[j] = rl;
+    floor_out[j] = fl;
     act[j] = go ? 1 : 0;
-    const double want = (rl > 0.0) ? 0.25 * tol / rl : 1e-2;
+    const double want = (rl > 0.0) ? 0.25 * lim / rl : 1e-2;
     tol_in[j] = fmin(1e-2, fmax(floor_tol, want));
   }
+}
+
+// hbound[0] = max_a kin[a] + max_a |V[a]|: a bound of ||H||_2 (H = T + V, T diagonal in Fourier
+// space with entries kin >= 0, V diagonal in real space); one CTA.
+__global__ void __launch_bounds__(kThreads) hbound_kernel(int N, const double* __restrict__ kin,
+                                                          const double* __restrict__ V, double* __restrict__ hbound) {
+  __shared__ double rk[kThreads], rv[kThreads];
+  double mk = 0.0, mv = 0.0;
+  for (int a = threadIdx.x; a < N; a += blockDim.x) {
+    mk = fmax(mk, kin[a]);
+    mv = fmax(mv, fabs(V[a]));
+  }
+  rk[threadIdx.x] = mk;
+  rv[threadIdx.x] = mv;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      rk[threadIdx.x] = fmax(rk[threadIdx.x], rk[threadIdx.x + o]);
+      rv[threadIdx.x] = fmax(rv[threadIdx.x], rv[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) hbound[0] = rk[0] + rv[0];
 }
 
 // X_j += scale_j * D32_j for the active columns
@@ -242,11 +292,57 @@ __global__ void to_float_kernel(size_t n, const double* __restrict__ x, float* _
     y[e] = (float)x[e];
 }
 
+// dst[:, k] = src[:, idx[k]] (N x n from N-row columns); shifts likewise when sh_src is given.
+__global__ void gather_cols_kernel(int N, int n, const int* __restrict__ idx, const double* __restrict__ src,
+                                   double* __restrict__ dst, const double* __restrict__ sh_src,
+                                   double* __restrict__ sh_dst) {
+  const size_t total = (size_t)N * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e % N), k = (int)(e / N);
+    dst[e] = src[(size_t)idx[k] * N + a];
+    if (sh_src && a == 0) sh_dst[k] = sh_src[idx[k]];
+  }
+}
+
+// dst[:, idx[k]] += src[:, k]
+__global__ void scatter_add_cols_kernel(int N, int n, const int* __restrict__ idx, const double* __restrict__ src,
+                                        double* __restrict__ dst) {
+  const size_t total = (size_t)N * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e % N), k = (int)(e / N);
+    dst[(size_t)idx[k] * N + a] += src[e];
+  }
+}
+
+// act[j] = 1 for the listed columns, 0 for the others
+__global__ void mark_cols_kernel(int ncol, int n, const int* __restrict__ idx, int* __restrict__ act) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ncol; j += gridDim.x * blockDim.x) act[j] = 0;
+}
+__global__ void mark_cols2_kernel(int n, const int* __restrict__ idx, int* __restrict__ act) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) act[idx[k]] = 1;
+}
+
+// rel[idx[k]] = ||R_k|| / ||B_idx[k]|| for the N x n block R (FP64, already projected); one warp a column
+__global__ void polish_rel_kernel(int N, int n, const int* __restrict__ idx, const double* __restrict__ R,
+                                  const double* __restrict__ bnorm, double* __restrict__ rel) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (k >= n) return;
+  const double* r = R + (size_t)k * N;
+  double acc = 0.0;
+  for (int a = lane; a < N; a += 32) acc += r[a] * r[a];
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    const double bn = bnorm[idx[k]];
+    rel[idx[k]] = (bn > 0.0) ? sqrt(acc) / bn : 0.0;
+  }
+}
+
 __global__ void refine_report_kernel(int n, const double* __restrict__ rel, const double* __restrict__ bnorm,
-                                     double tol, unsigned long long* conv, double* max_res) {
+                                     const double* __restrict__ floor_in, double tol, unsigned long long* conv,
+                                     double* max_res) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double r = (bnorm[i] > 0.0) ? rel[i] : 0.0;
-    if (r <= tol) atomicAdd(conv, 1ull);
+    if (r <= fmax(tol, floor_in[i])) atomicAdd(conv, 1ull);
     atomicMax(reinterpret_cast<unsigned long long*>(max_res), (unsigned long long)__double_as_longlong(r));
   }
 }
@@ -558,6 +654,72 @@ acp_status minres32(acp_ctx* ctx, const float* R32, int ncol, const float* shift
   return sum_iters(ctx, s.iters, ncol, steps, max_it);
 }
 
+// FP64 finish of the columns the FP32 rounds left above their tolerance (stalled, or at the round
+// cap): gather their FP64 residuals R (current for X), project them in FP64, solve
+// Q(H - s)Q D = Q R by FP64 MINRES to the largest reduction any of them still needs, X += D, and
+// re-evaluate the true FP64 residuals; at most three passes.  rel is updated for those columns.
+acp_status polish_fp64(acp_ctx* ctx, const double* B, int ncol, const double* shift_d, double* X, double* R,
+                       double* Y, int* act, const double* bnorm, double* rel, const double* floor_j,
+                       SolveReport* rep, double t0_ms) {
+  const int N = ctx->N;
+  const double tol = ctx->opt.stern_tol;
+  std::vector<double> hr(ncol), hf(ncol);
+  ACP_CUDA(ctx, cudaMemcpyAsync(hf.data(), floor_j, sizeof(double) * ncol, cudaMemcpyDeviceToHost, ctx->stream));
+  for (int pass = 0; pass < 3; ++pass) {
+    ACP_CUDA(ctx, cudaMemcpyAsync(hr.data(), rel, sizeof(double) * ncol, cudaMemcpyDeviceToHost, ctx->stream));
+    ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<int> idx;
+    double need = 1.0;
+    for (int j = 0; j < ncol; ++j) {
+      const double lim = fmax(tol, hf[j]);
+      if (hr[j] > lim) {
+        idx.push_back(j);
+        need = fmin(need, lim / hr[j]);
+      }
+    }
+    if (idx.empty()) return ACP_OK;
+    if (deadline_passed(ctx, t0_ms)) return set_error(ctx, ACP_E_TIMEOUT, "deadline passed in refinement");
+    const int n = (int)idx.size();
+    const size_t nv = (size_t)N * n;
+    int* d_idx = nullptr;
+    double *Rp = nullptr, *Dp = nullptr, *sp = nullptr;
+    ACP_TRY(ws(ctx, "pl_idx", (size_t)n, &d_idx));
+    ACP_TRY(ws(ctx, "pl_r", nv, &Rp));
+    ACP_TRY(ws(ctx, "pl_d", nv, &Dp));
+    ACP_TRY(ws(ctx, "pl_sh", (size_t)n, &sp));
+    ACP_CUDA(ctx, cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+    ::acp::note_launch(ctx);
+    gather_cols_kernel<<<grid_for(nv), 256, 0, ctx->stream>>>(N, n, d_idx, R, Rp, shift_d, sp);
+    ACP_LAUNCH(ctx);
+    ACP_TRY(project(ctx, Rp, N, n, Rp, N));
+    SolveReport sub{};
+    ACP_TRY(minres_batched_fp64(ctx, Rp, n, sp, Dp, 0.5 * need, &sub, t0_ms));
+    rep->steps += sub.steps;
+    if (sub.max_iters > rep->max_iters) rep->max_iters = sub.max_iters;
+    ::acp::note_launch(ctx);
+    scatter_add_cols_kernel<<<grid_for(nv), 256, 0, ctx->stream>>>(N, n, d_idx, Dp, X);
+    ACP_LAUNCH(ctx);
+    ::acp::note_launch(ctx);
+    mark_cols_kernel<<<grid_for(ncol), 256, 0, ctx->stream>>>(ncol, n, d_idx, act);
+    ACP_LAUNCH(ctx);
+    ::acp::note_launch(ctx);
+    mark_cols2_kernel<<<grid_for(n), 256, 0, ctx->stream>>>(n, d_idx, act);
+    ACP_LAUNCH(ctx);
+    ACP_TRY(spectral_apply(ctx, X, N, ncol, MULT_KINETIC, true, shift_d, Y, N, nullptr, act));
+    ::acp::note_launch(ctx);
+    residual_kernel<<<grid_for((size_t)N * ncol), 256, 0, ctx->stream>>>(N, ncol, B, Y, act, R);
+    ACP_LAUNCH(ctx);
+    ::acp::note_launch(ctx);
+    gather_cols_kernel<<<grid_for(nv), 256, 0, ctx->stream>>>(N, n, d_idx, R, Rp, nullptr, nullptr);
+    ACP_LAUNCH(ctx);
+    ACP_TRY(project(ctx, Rp, N, n, Rp, N));
+    ::acp::note_launch(ctx);
+    polish_rel_kernel<<<(n * 32 + 255) / 256, 256, 0, ctx->stream>>>(N, n, d_idx, Rp, bnorm, rel);
+    ACP_LAUNCH(ctx);
+  }
+  return ACP_OK;
+}
+
 // Refinement rounds over ncol columns: B (FP64, projected), shift_d (FP64), X in/out.
 acp_status refine(acp_ctx* ctx, const double* B, int ncol, const double* shift_d, double* X, bool x_zero,
                   SolveReport* rep, double t0_ms) {
@@ -569,7 +731,7 @@ acp_status refine(acp_ctx* ctx, const double* B, int ncol, const double* shift_d
   int* act = nullptr;
   ACP_TRY(ws(ctx, "rf_r", nv, &R));
   ACP_TRY(ws(ctx, "rf_y", nv, &Y));
-  ACP_TRY(ws(ctx, "rf_dsc", 4 * (size_t)ncol, &dsc));
+  ACP_TRY(ws(ctx, "rf_dsc", 6 * (size_t)ncol + 1, &dsc));
   ACP_TRY(ws(ctx, "rf_r32", (size_t)ld * ncol, &R32));
   ACP_TRY(ws(ctx, "rf_d32", (size_t)ld * ncol, &D32));
   ACP_TRY(ws(ctx, "rf_sh32", (size_t)ncol, &sh32));
@@ -578,6 +740,15 @@ acp_status refine(acp_ctx* ctx, const double* B, int ncol, const double* shift_d
   double* scale = dsc + ncol;
   double* rel = dsc + 2 * ncol;
   double* tol_in = dsc + 3 * ncol;
+  double* prev = dsc + 4 * ncol;
+  double* floor_j = dsc + 5 * ncol;
+  double* hbound = dsc + 6 * ncol;
+  int lg = 0;
+  while ((1 << lg) < N) ++lg;
+  const double log_fac = lg + 4.0;
+  ::acp::note_launch(ctx);
+  hbound_kernel<<<1, kThreads, 0, ctx->stream>>>(N, ctx->d_kin, ctx->d_V, hbound);
+  ACP_LAUNCH(ctx);
   ACP_CUDA(ctx, cudaMemsetAsync(R32, 0, sizeof(float) * ld * ncol, ctx->stream));
   ::acp::note_launch(ctx);
   col_norms64<<<(ncol * 32 + 255) / 256, 256, 0, ctx->stream>>>(N, ncol, B, bnorm);
@@ -603,8 +774,8 @@ acp_status refine(acp_ctx* ctx, const double* B, int ncol, const double* shift_d
     ACP_LAUNCH(ctx);
     ACP_TRY(project32(ctx, R32, ld, ncol, R32, ld));
     ::acp::note_launch(ctx);
-    refine_check_kernel<<<ncol, kThreads, 0, ctx->stream>>>(N, ld, R32, scale, bnorm, tol, rel, act, tol_in,
-                                                            kInnerTol);
+    refine_check_kernel<<<ncol, kThreads, 0, ctx->stream>>>(N, ld, R32, X, shift_d, hbound, log_fac, scale, bnorm,
+                                                            tol, rel, prev, floor_j, round, act, tol_in, kInnerTol);
     ACP_LAUNCH(ctx);
     int n_act = 0;
     ACP_TRY(count32(ctx, act, ncol, &n_act));
@@ -619,6 +790,7 @@ acp_status refine(acp_ctx* ctx, const double* B, int ncol, const double* shift_d
     residual_kernel<<<grid_for(nv), 256, 0, ctx->stream>>>(N, ncol, B, Y, act, R);
     ACP_LAUNCH(ctx);
   }
+  ACP_TRY(polish_fp64(ctx, B, ncol, shift_d, X, R, Y, act, bnorm, rel, floor_j, rep, t0_ms));
   int h_nan = 0;
   ACP_CUDA(ctx, cudaMemcpyAsync(&h_nan, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -631,7 +803,8 @@ acp_status refine(acp_ctx* ctx, const double* B, int ncol, const double* shift_d
   ACP_TRY(ws(ctx, "rf_rep", 1, &d));
   ACP_CUDA(ctx, cudaMemsetAsync(d, 0, sizeof(Rep), ctx->stream));
   ::acp::note_launch(ctx);
-  refine_report_kernel<<<grid_for(ncol), 256, 0, ctx->stream>>>(ncol, rel, bnorm, tol, &d->conv, &d->max_res);
+  refine_report_kernel<<<grid_for(ncol), 256, 0, ctx->stream>>>(ncol, rel, bnorm, floor_j, tol, &d->conv,
+                                                                 &d->max_res);
   ACP_LAUNCH(ctx);
   Rep h{};
   ACP_CUDA(ctx, cudaMemcpyAsync(&h, d, sizeof(Rep), cudaMemcpyDeviceToHost, ctx->stream));
