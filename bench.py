@@ -1,7 +1,10 @@
 #!/usr/bin/env python3
 """Benchmark: Sternheimer (shift, right-hand side) pairs solved per second and dynamical-matrix
 time of the ACP method on one GB300, on the 1D rHF chain of 128 atoms (N = 5120 grid points,
-mixed charges Z in {1, 2}, 192 occupied orbitals, 128 perturbations, 16 Chebyshev nodes).
+mixed charges Z in {1, 2}, 192 occupied orbitals, 128 perturbations).  The timed settings (20
+Chebyshev nodes, id_tol 1e-9, Alg. 4 delta 1e-9) are the cheapest tried that meet the 1e-5
+relative phonon-frequency bar against the oracle's exact D; the configuration's own 16 nodes miss
+it (error 5e-5) and are reported as a labelled comparison.
 
 A step is one pass of the whole hot path: perturbation potentials g and B = K^{-1} G, the
 adaptive Alg. 4 (sketch + pivoted QR + interpolation vectors, multi-shift MINRES on the
@@ -34,7 +37,11 @@ sys.path.insert(0, ROOT)
 METRIC = "Sternheimer RHS solved/s and dynamical-matrix time, ACP forms vs plain FP64, 1 GB300"
 UNIT = "RHS/s"
 CONFIG = 2
-ACP_PARAMS = dict(id_tol=1e-8, n_cheb=16, sketch_r=8, dyson_tol=1e-6, dyson_maxit=20, stern_tol=1e-11)
+ACP_PARAMS = dict(id_tol=1e-9, n_cheb=20, sketch_r=8, dyson_tol=1e-9, dyson_maxit=20, stern_tol=1e-11)
+# the configuration's stated node count (misses the 1e-5 bar; a labelled comparison figure)
+CONFIG_STATED = dict(id_tol=1e-8, n_cheb=16, dyson_tol=1e-6)
+# selected points of the first Alg. 4 iteration whose compressed solves one oracle sample times
+ORACLE_SAMPLE_MU = 8
 
 
 def workload_name():
@@ -179,10 +186,11 @@ PRECISION = 0
 USE_GRAPHS = 0
 
 
-def make_context(P, s, gs, om, V, psi):
-    o = P.options(method=P.ACP_METHOD_ACP, occ=float(s.occ), sketch=om, id_tol=ACP_PARAMS["id_tol"],
-                  n_cheb=ACP_PARAMS["n_cheb"], dyson_tol=ACP_PARAMS["dyson_tol"],
-                  dyson_maxit=ACP_PARAMS["dyson_maxit"], stern_tol=ACP_PARAMS["stern_tol"],
+def make_context(P, s, gs, om, V, psi, **override):
+    prm = {**ACP_PARAMS, **override}
+    o = P.options(method=P.ACP_METHOD_ACP, occ=float(s.occ), sketch=om, id_tol=prm["id_tol"],
+                  n_cheb=prm["n_cheb"], dyson_tol=prm["dyson_tol"],
+                  dyson_maxit=prm["dyson_maxit"], stern_tol=prm["stern_tol"],
                   precision=PRECISION, use_graphs=USE_GRAPHS)
     n, L, _ = grid_args(s)
     return P.Context(n, L, s.kappa, s.scale, V, psi, gs.eps[: gs.n_orb], o)
@@ -209,7 +217,8 @@ def run_gpu(args):
     stream = ctx.stream
 
     def step():
-        D, st = ctx.dynamical_matrix(R, Z, sig, rho, allow_noconv=True)
+        # any status but ACP_OK (an unconverged solve included) raises: no step is timed on it
+        D, st = ctx.dynamical_matrix(R, Z, sig, rho)
         w = ctx.phonons(D)
         return D, w, st
 
@@ -254,7 +263,7 @@ def run_gpu(args):
             psi_d.copy_(psi_h, non_blocking=True)
             rho_d.copy_(rho_h, non_blocking=True)
         ctx.update(V_d, psi_d, gs.eps[: gs.n_orb])
-        D2, st2 = ctx.dynamical_matrix(R, Z, sig, rho_d, allow_noconv=True)
+        D2, st2 = ctx.dynamical_matrix(R, Z, sig, rho_d)
         w2 = ctx.phonons(D2)
         e2e_pairs += st2["rhs_solved"]
     torch.cuda.synchronize()
@@ -310,7 +319,7 @@ def run_gpu(args):
                              "mixed: FP32 MINRES + 3xTF32 tcgen05 projector + FP64 refinement")},
         "rhs_pairs_per_step": pairs / args.steps, "n_mu": st["n_mu"], "alg4_iters": st["outer_iters"],
         "lanczos_steps_per_step": sum(x["lanczos_steps"] for x in stats) / len(stats),
-        "accuracy": accuracy(D, w),
+        "accuracy": accuracy(D, w, ctx, s),
         "solve_ms_per_step": round(sum(x["ms_solve"] for x in stats) / len(stats), 2),
         "compress_ms_per_step": round(sum(x["ms_compress"] for x in stats) / len(stats), 2),
         "e2e": {"value": round(e2e_pairs_all / e2e_max, 2), "unit": UNIT,
@@ -327,6 +336,25 @@ def run_gpu(args):
     return line
 
 
+def timed_once(P, s, gs, om, V, psi, rho, R, Z, sig, **override):
+    """D time (CUDA events, one warm run first), refined pairs/s and accuracy of one setting."""
+    import torch
+    ctx = make_context(P, s, gs, om, V, psi, **override)
+    ctx.dynamical_matrix(R, Z, sig, rho)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    D, st = ctx.dynamical_matrix(R, Z, sig, rho)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    w = ctx.phonons(D)
+    ms = e0.elapsed_time(e1)
+    res = {"D_ms": round(ms, 1), "rhs_solved": st["rhs_solved"], "rhs_per_s": round(st["rhs_solved"] / (ms * 1e-3), 1),
+           "n_mu": st["n_mu"], "alg4_iters": st["outer_iters"], "accuracy": accuracy(D, w, ctx, s)}
+    ctx.close()
+    return res
+
+
 def compare_forms(P, s, gs, om, V, psi, rho, R, Z, sig):
     """Dynamical-matrix time of the other ACP arithmetic (FP64 when the timed form is mixed, and
     vice versa), one warm run each, and of plain FP64 DFPT (Alg. 1 + GMRES on the Dyson equation)
@@ -341,22 +369,16 @@ def compare_forms(P, s, gs, om, V, psi, rho, R, Z, sig):
     saved = PRECISION
     PRECISION = other
     try:
-        ctx = make_context(P, s, gs, om, V, psi)
-        ctx.dynamical_matrix(R, Z, sig, rho, allow_noconv=True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(ctx.stream)
-        D, st = ctx.dynamical_matrix(R, Z, sig, rho, allow_noconv=True)
-        e1.record(ctx.stream)
-        torch.cuda.synchronize()
-        w = ctx.phonons(D)
         key = "acp_fp64" if other == 0 else "acp_mixed"
-        out[key] = {"D_ms": round(e0.elapsed_time(e1), 1), "rhs_solved": st["rhs_solved"],
-                    "rhs_per_s": round(st["rhs_solved"] / (e0.elapsed_time(e1) * 1e-3), 1),
-                    "accuracy": accuracy(D, w)}
-        ctx.close()
+        out[key] = timed_once(P, s, gs, om, V, psi, rho, R, Z, sig)
     finally:
         PRECISION = saved
+    if WORKLOAD == "c2":
+        out["acp_config_stated_nc16"] = dict(
+            timed_once(P, s, gs, om, V, psi, rho, R, Z, sig, **CONFIG_STATED),
+            settings=f"N_c={CONFIG_STATED['n_cheb']}, id_tol={CONFIG_STATED['id_tol']:g}, "
+                     f"delta={CONFIG_STATED['dyson_tol']:g} (the configuration's node count), "
+                     + ("mixed" if PRECISION else "FP64"))
     o = P.options(method=P.ACP_METHOD_PLAIN, occ=float(s.occ), stern_tol=ACP_PARAMS["stern_tol"],
                   dyson_tol=1e-10, dyson_maxit=80, precision=0)
     n, L, _ = grid_args(s)
@@ -365,7 +387,7 @@ def compare_forms(P, s, gs, om, V, psi, rho, R, Z, sig):
     Gs = G[:4].contiguous()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    U, st = ctxp.dyson_solve(Gs, allow_noconv=True)
+    U, st = ctxp.dyson_solve(Gs)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     out["plain_fp64"] = {"sample_columns": 4, "sample_ms": round(dt * 1e3, 1),
@@ -375,11 +397,26 @@ def compare_forms(P, s, gs, om, V, psi, rho, R, Z, sig):
     return out
 
 
-def accuracy(D, w):
+def _projected_omega(ctx, D, n_atoms, dim):
+    """Frequencies of P D P, P = I - T T^T removing the dim rigid translations (the acoustic sum
+    rule imposed by projection, the reading of Table 2's phonon errors), by the library's
+    eigensolver."""
+    import numpy as np
+    n = n_atoms * dim
+    T = np.zeros((n, dim))
+    for a in range(dim):
+        T[a::dim, a] = 1.0 / np.sqrt(n_atoms)
+    Pm = np.eye(n) - T @ T.T
+    return ctx.phonons(Pm @ np.asarray(D) @ Pm)
+
+
+def accuracy(D, w, ctx, s):
     """Errors against exact references written by the oracle: for the 128-atom chain
-    (tests/golden/c2_exact_dmat.npz) the relative Frobenius error of D and max |omega -
-    omega_ref| / max |omega_ref|; for the 2D lattice (tests/golden/c3_exact_dcols.npz, a sample of
-    exact columns of D) the relative Frobenius error of those columns.  None otherwise."""
+    (tests/golden/c2_exact_dmat.npz) the relative Frobenius error of D, the relative phonon-frequency
+    error max |omega - omega_ref| / max |omega_ref| with the translations projected out of both
+    (Table 2's reading, ``omega_rel``) and without (``omega_rel_unprojected``, dominated by the
+    acoustic mode); for the 2D lattice (tests/golden/c3_exact_dcols.npz, a sample of exact
+    columns of D) the relative Frobenius error of those columns.  None otherwise."""
     import numpy as np
     if WORKLOAD == "c3":
         path = os.path.join(ROOT, "tests", "golden", "c3_exact_dcols.npz")
@@ -393,8 +430,12 @@ def accuracy(D, w):
     if WORKLOAD != "c2" or not os.path.exists(path):
         return None
     ref = np.load(path)
+    wp = _projected_omega(ctx, D, s.n_atoms, s.dim)
+    wpr = _projected_omega(ctx, ref["D"], s.n_atoms, s.dim)
     return {"D_rel_fro": float(np.linalg.norm(D - ref["D"]) / np.linalg.norm(ref["D"])),
-            "omega_rel": float(np.abs(w - ref["omega"]).max() / np.abs(ref["omega"]).max())}
+            "omega_rel": float(np.abs(wp - wpr).max() / np.abs(wpr).max()),
+            "omega_rel_unprojected": float(np.abs(w - ref["omega"]).max() / np.abs(ref["omega"]).max()),
+            "bar": 1e-5}
 
 
 # ---- configuration 4: many systems through the batched form ------------------------------------
@@ -517,25 +558,25 @@ class OracleArm:
         self.A.compressed_solves(self.m, self.comp.Xi[:, :n_mu], self.nodes, tol=ACP_PARAMS["stern_tol"])
         return time.perf_counter() - t0
 
-    def sample(self, seconds_hint=20.0):
+    def sample(self, reps=1):
+        """One sample = the compressed solves of the first ORACLE_SAMPLE_MU selected points (all
+        N_c shifts), timed reps times; the same sample serves cpu_baseline and the reference arm."""
         n_total = self.comp.Xi.shape[1]
-        n_mu = 2
-        dt = self.solve(n_mu)
-        # grow the sample toward the time hint
-        while dt < 0.5 * seconds_hint and n_mu < n_total:
-            n_mu = min(n_total, max(n_mu * 2, int(n_mu * seconds_hint / max(dt, 1e-3) * 0.8)))
-            dt = self.solve(n_mu)
-        pairs = n_mu * len(self.nodes)
+        n_mu = min(ORACLE_SAMPLE_MU, n_total)
+        dt = sum(self.solve(n_mu) for _ in range(reps))
+        pairs = reps * n_mu * len(self.nodes)
         return {"value": round(pairs / dt, 3), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                "sample": (f"compressed Sternheimer solves (Eq. eqncompressU) for {n_mu} of the {n_total} "
-                           f"selected points x {len(self.nodes)} Chebyshev shifts of the first Alg. 4 iteration "
-                           f"({pairs} pairs in {dt:.1f} s; the pivoted QR took {self.t_comp:.1f} s and is not "
-                           f"counted)")}
+                "sample": (f"compressed Sternheimer solves (Eq. eqncompressU, MINRES to {ACP_PARAMS['stern_tol']:g}) "
+                           f"for the first {n_mu} of the {n_total} selected points x {len(self.nodes)} Chebyshev "
+                           f"shifts of the first Alg. 4 iteration, {reps} time(s) ({pairs} pairs in {dt:.1f} s; "
+                           f"the pivoted QR took {self.t_comp:.1f} s and is not counted)")}
 
 
 def cpu_baseline(seconds):
     try:
-        return OracleArm().sample(seconds)
+        arm = OracleArm()
+        t = arm.solve(min(ORACLE_SAMPLE_MU, arm.comp.Xi.shape[1]))
+        return arm.sample(reps=max(1, min(4, int(seconds / max(t, 1e-3)))))
     except Exception as e:  # the baseline is informative; it must not sink the GPU line
         return {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
 
@@ -551,7 +592,7 @@ def run_reference(args):
     samples, times = [], []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        samples.append(arm.sample(args.cpu_seconds / max(1, args.steps)))
+        samples.append(arm.sample())
         times.append(time.perf_counter() - t0)
     v = statistics.median([x["value"] for x in samples])
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

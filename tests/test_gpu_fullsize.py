@@ -4,10 +4,10 @@ perturbations), in the launch configuration bench.py times.
 * Plain path: sampled columns of U = chi G (GMRES per column is independent, so a column
   sample is an exact sub-problem) against the oracle's sum-over-states chi0 + GMRES.
 * ACP: the dynamical matrix against the oracle's exact D (tests/golden/c2_exact_dmat.npz,
-  written by tests/golden/make_c2_reference.py from the oracle only).  ACP is an approximation:
-  the bound is its own error budget, the Chebyshev interpolation error rho^-N_c with
-  rho = a + sqrt(a^2 - 1), a = 1 + 2 gap / (eps_N - eps_1) (Sec. 3.1), amplified by the
-  ~3e4-fold cancellation in D, plus the compression threshold.
+  written by tests/golden/make_c2_reference.py from the oracle only), within the 1e-5 relative
+  phonon-frequency bar.  ACP is an approximation: its error budget is the Chebyshev
+  interpolation error rho^-N_c with rho = a + sqrt(a^2 - 1), a = 1 + 2 gap / (eps_N - eps_1)
+  (Sec. 3.1), amplified by the ~3e4-fold cancellation in D, plus the compression threshold.
 * Properties that hold at any size: the interpolation property Xi(r_mu, :) = I of the
   full-size compression and N_mu between 3 and 8 times N_e (Table 2 reports 4-6 N_e).
 """
@@ -62,20 +62,32 @@ def test_c2_compression_properties(c2):
 
 
 @pytest.mark.skipif(not os.path.exists(GOLDEN), reason="exact reference not generated")
-@pytest.mark.parametrize("eps,nc,delta,bound", [(1e-8, 16, 1e-6, 2e-2), (1e-10, 24, 1e-11, 2e-4)])
-def test_c2_acp_dynamical_matrix_vs_exact(c2, eps, nc, delta, bound):
+@pytest.mark.parametrize("eps,nc,delta,precision,bound", [(1e-9, 20, 1e-9, 1, 1e-5), (1e-10, 24, 1e-11, 0, 1e-7)])
+def test_c2_acp_dynamical_matrix_vs_exact(c2, eps, nc, delta, precision, bound):
+    """The accelerated forms meet the 1e-5 relative phonon-frequency bar (frequencies with the
+    acoustic sum rule imposed by projection, the reading Table 2 fixes; oracle.dmat.phonon_error)
+    and D the same bound, at the benchmark's settings (mixed, N_c = 20) and at tighter FP64
+    settings.  The error follows the Chebyshev interpolation budget rho^-N_c of Sec. 3.1 (rho =
+    2.71 at this band and gap), amplified by the ~3e4-fold cancellation in D: measured D errors are
+    5.7e-5 at N_c = 16 (the configuration's count, which misses the bar), 5.9e-7 at 20, 1.6e-8 at
+    24."""
     import torch
+
+    from oracle import dmat as DM
     s, gs, m = c2
     ref = np.load(GOLDEN)
     om = W.srft_sketch(s.n_pert, 8, 2)
-    ctx = context("c2", method=1, sketch=om, id_tol=eps, n_cheb=nc, dyson_tol=delta, dyson_maxit=25)
+    ctx = context("c2", method=1, sketch=om, id_tol=eps, n_cheb=nc, dyson_tol=delta, dyson_maxit=25,
+                  precision=precision, stern_tol=1e-11)
     rho = torch.tensor(gs.rho, dtype=torch.float64, device="cuda")
-    D, st = ctx.dynamical_matrix(s.R[:, 0], s.Z, s.sigma, rho, allow_noconv=True)
-    w = ctx.phonons(D)
-    err = np.abs(w - ref["omega"]).max() / np.abs(ref["omega"]).max()
+    D, st = ctx.dynamical_matrix(s.R[:, 0], s.Z, s.sigma, rho)
     # interpolation error budget of Sec. 3.1 for this band and gap
     a = 1 + 2 * gs.gap / (gs.eps[gs.n_orb - 1] - gs.eps[0])
     rho_c = a + np.sqrt(a * a - 1)
-    assert rho_c ** -nc < 1e-5
+    assert rho_c ** -nc < 1e-7
+    _, err = DM.phonon_error(D, ref["D"], s.n_atoms, 1)
     assert err < bound
     assert rel(D, ref["D"]) < bound
+    # the library's own eigensolver agrees with the oracle's on the same D
+    w = ctx.phonons(D)
+    assert np.abs(w - DM.phonons(D)[0]).max() <= 1e-10 * np.abs(w).max()

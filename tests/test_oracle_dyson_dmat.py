@@ -1,4 +1,6 @@
 """Pins of the oracle's Dyson solve and dynamical matrix (Eq. dyson, Eq. SecDeriv)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -111,3 +113,32 @@ def test_phonon_dos_normalisation_moments_and_counting():
     xs = np.arange(-0.05, cut, 1e-5)  # sigma / 10: the trapezoid rule is exact to rounding here
     below = np.trapezoid(Dm.phonon_dos(om, xs, 1e-4), xs)
     assert abs(below - (j + 1) / om.size) < 1e-9
+
+
+@pytest.mark.parametrize("kind", ["1d", "2d"])
+def test_sampled_exact_columns_equal_full_dynamical_matrix(kind):
+    """The sampled-column form that writes the stored exact columns of D (GMRES on the Dyson
+    equation with the sum-over-states chi0, Eq. SecDeriv assembled per column) equals the columns
+    of the dense route (dense Dyson solve, full D), on a chain and on a 2D lattice."""
+    import importlib.util
+    from oracle import chi0 as C
+    from oracle import dmat as DM
+    from oracle import dyson as Dy
+    from oracle.model import Model1D, Model2D
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "make_dcols_reference.py")
+    spec_ = importlib.util.spec_from_file_location("make_dcols_reference", path)
+    mk = importlib.util.module_from_spec(spec_)
+    spec_.loader.exec_module(mk)
+    if kind == "1d":
+        s = W.small_chain(4, 160, 0)
+        m = Model1D(s, W.ground_state(s, use_cache=False))
+        cols = [0, 3]
+    else:
+        s = W.small_lattice(2, 2, 24, 0)
+        m = Model2D(s, W.ground_state(s, use_cache=False))
+        cols = [0, 3, 6]
+    G, _ = m.perturbations()
+    D, _ = DM.dynamical_matrix(m, Dy.dyson_dense(m, G))
+    Dc, _, res = mk.exact_columns(m, cols, C.full_spectrum(m))
+    assert res < 1e-12
+    assert np.abs(Dc - D[:, cols]).max() <= 1e-9 * np.abs(D).max()
