@@ -23,7 +23,8 @@ import scipy.linalg as sla
 
 from .systems import System
 
-CACHE_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cache")
+# converged potentials, one file per system key (ACP_GS_CACHE names another directory)
+CACHE_DIR = os.environ.get("ACP_GS_CACHE") or os.path.join(os.path.dirname(os.path.abspath(__file__)), "cache")
 
 
 @dataclasses.dataclass

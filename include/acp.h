@@ -310,8 +310,9 @@ acp_status acp_cnn_get_weights(acp_ctx* ctx, float* w_h);
    call on each device looks up the array's device address (cudaGetSymbolAddress); make that
    first call before any stream capture.
    Errors: ACP_E_ARG (null pointer, n_grid, n_orb or h not positive, ncol negative, or
-   n_orb * ncol above the maximum; nothing is enqueued), ACP_E_CUDA (the address lookup or a
-   launch failed). */
+   n_orb * ncol above the maximum; nothing is enqueued), ACP_E_CUDA (a CUDA error was already
+   pending on entry, from earlier work of the process, and nothing is enqueued; or the address
+   lookup or one of the two launches failed). */
 acp_status acp_project_noalloc(const double* psi_d, int n_grid, int n_orb, double h, const double* X_d, int ncol,
                                double* Y_d, void* stream);
 

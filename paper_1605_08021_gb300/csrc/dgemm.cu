@@ -224,6 +224,9 @@ extern "C" acp_status acp_project_noalloc(const double* psi_d, int n_grid, int n
   if (!psi_d || !X_d || !Y_d || n_grid < 1 || n_orb < 1 || ncol < 0 || !(h > 0.0)) return ACP_E_ARG;
   if (ncol == 0) return ACP_OK;
   if ((size_t)n_orb * (size_t)ncol > kNoAllocElems) return ACP_E_ARG;
+  // an error left by earlier, unrelated work would otherwise be read (and cleared) by the launch
+  // checks below and reported as this call's; refuse to enqueue onto a context in that state
+  if (cudaPeekAtLastError() != cudaSuccess) return ACP_E_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -248,6 +251,7 @@ extern "C" acp_status acp_project_noalloc(const double* psi_d, int n_grid, int n
   // C = h Psi^T X: beta = 0, so every entry is written and nothing needs clearing beforehand
   launch<true, false>(dim3((n_orb + BM - 1) / BM, (ncol + BN - 1) / BN), s, n_orb, ncol, n_grid, h, psi_d, n_grid,
                       X_d, n_grid, 0.0, C, n_orb, nullptr, 0);
+  if (cudaGetLastError() != cudaSuccess) return ACP_E_CUDA;  // the first GEMM did not launch
   if (Y_d != X_d) {
     if (cudaMemcpyAsync(Y_d, X_d, sizeof(double) * (size_t)n_grid * ncol, cudaMemcpyDeviceToDevice, s) !=
         cudaSuccess) {
@@ -258,6 +262,6 @@ extern "C" acp_status acp_project_noalloc(const double* psi_d, int n_grid, int n
   // Y -= Psi C
   launch<false, false>(dim3((n_grid + BM - 1) / BM, (ncol + BN - 1) / BN), s, n_grid, ncol, n_orb, -1.0, psi_d,
                        n_grid, C, n_orb, 1.0, Y_d, n_grid, nullptr, 0);
-  if (cudaGetLastError() != cudaSuccess) return ACP_E_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return ACP_E_CUDA;  // the second GEMM did not launch
   return ACP_OK;
 }
