@@ -235,6 +235,14 @@ acp_status acp_project(acp_ctx* ctx, const double* X_d, int ncol, double* Y_d);
    X_d.  Errors: ACP_E_TIMEOUT if a tensor-core pipeline wait ran out (the result is then invalid). */
 acp_status acp_project_mixed(acp_ctx* ctx, const double* X_d, int ncol, double* Y_d);
 
+/* Failure-detection self-test of the bounded device waits (no counterpart in the paper).  Runs one
+   tensor-core projector GEMM on 128 zero columns whose TMA loads are withheld, so that its
+   mbarrier waits can never complete: each wait gives up after wait_s seconds (0 < wait_s <= 1),
+   the kernel skips its MMAs and epilogue, frees its tensor memory and sets the device status word,
+   and the call returns ACP_E_TIMEOUT; the context stays usable.  ACP_OK would mean a wait did not
+   run out.  Errors: ACP_E_ARG (wait_s outside (0, 1]), ACP_E_CUDA, ACP_E_OOM. */
+acp_status acp_selftest_wait_timeout(acp_ctx* ctx, double wait_s);
+
 /* Y = K X (kernel_op = 1) or K^{-1} X (kernel_op = -1): spectral Yukawa convolution. */
 acp_status acp_kernel_apply(acp_ctx* ctx, const double* X_d, int ncol, int kernel_op, double* Y_d);
 

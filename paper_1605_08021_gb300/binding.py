@@ -103,6 +103,7 @@ def load():
         "acp_project_mixed": (I, [P, P, I, P]),
         "acp_project_noalloc": (I, [P, I, I, c_double, P, I, P, P]),
         "acp_kernel_apply": (I, [P, P, I, I, P]),
+        "acp_selftest_wait_timeout": (I, [P, c_double]),
         "acp_sternheimer_solve": (I, [P, P, I, D, P, POINTER(Stats)]),
         "acp_compress": (I, [P, P, I, I, POINTER(c_int), POINTER(c_int), P, D]),
         "acp_cnn_set_weights": (I, [P, POINTER(ctypes.c_float), c_longlong]),
@@ -397,6 +398,10 @@ class Context:
         self._call(self.lib.acp_sternheimer_solve(self.ptr, _tptr(Bm), Bm.shape[0], _dptr(sh), _tptr(X),
                                                   ctypes.byref(st)), allow_noconv)
         return X, st.as_dict()
+
+    def selftest_wait_timeout(self, wait_s):
+        """Status name of acp_selftest_wait_timeout (ACP_E_TIMEOUT when the bounded waits work)."""
+        return STATUS.get(self.lib.acp_selftest_wait_timeout(self.ptr, float(wait_s)))
 
     def compress(self, G, cap=None):
         import torch

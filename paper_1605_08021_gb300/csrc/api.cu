@@ -578,6 +578,12 @@ acp_status acp_project_mixed(acp_ctx* ctx, const double* X_d, int ncol, double* 
   return ACP_OK;
 }
 
+acp_status acp_selftest_wait_timeout(acp_ctx* ctx, double wait_s) {
+  ACP_TRY(check_ctx(ctx));
+  if (!(wait_s > 0.0) || wait_s > 1.0) return set_error(ctx, ACP_E_ARG, "wait_s must lie in (0, 1]");
+  return tc_selftest_timeout(ctx, (uint64_t)(wait_s * 1e9));
+}
+
 acp_status acp_kernel_apply(acp_ctx* ctx, const double* X_d, int ncol, int kernel_op, double* Y_d) {
   ACP_TRY(check_ctx(ctx));
   if (!X_d || !Y_d || ncol < 0 || (kernel_op != 1 && kernel_op != -1))

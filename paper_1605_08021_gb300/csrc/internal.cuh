@@ -245,6 +245,7 @@ acp_status spectral32_apply(acp_ctx* ctx, const float* X, int ldx, int ncol, con
 acp_status mixed_prepare(acp_ctx* ctx);
 acp_status project32(acp_ctx* ctx, const float* X, int ldx, int ncol, float* Y, int ldy);
 acp_status tc_check(acp_ctx* ctx);
+acp_status tc_selftest_timeout(acp_ctx* ctx, uint64_t wait_ns);
 acp_status project_mixed64(acp_ctx* ctx, const double* X, int ncol, double* Y);
 
 // cnn.cu: the learned initial guess of the 2D Sternheimer solves.  cnn_set_weights copies the

@@ -52,31 +52,41 @@ int grid_for(size_t total) {
 }
 
 // ---- FP32 single-shift batched MINRES -----------------------------------------------------
+// Solve state of the n columns being iterated (compact index j); the caller's blocks (right-hand
+// sides R, corrections D, iteration counts) keep their own column order, map[j] being column j's
+// index there.  When most columns have converged the state is gathered into a smaller set.
 struct M32 {
-  float *V, *Vp, *P, *W1, *W2;         // ld x ncol
-  float *alpha, *beta;                 // ncol (Lanczos coefficients, read by the spectral kernel)
+  float *V, *Vp, *P, *W1, *W2;         // ld x n
+  float *alpha, *beta;                 // n (Lanczos coefficients, read by the spectral kernel)
   double *beta1, *cs, *sn, *dbar, *epsln, *phibar;
-  const double* tolc;                  // per-column relative tolerance (nullable: the scalar one)
-  int *active, *iters;
+  double* tolc;                        // n: relative tolerance of each column
+  float* shift;                        // n
+  int *active, *iters;                 // n
+  int* map;                            // n: column in the caller's blocks
+  int* iters_out;                      // iteration count by the caller's column
   int ld;
 };
 
+// Column j starts from R[:, map[j]] / ||R[:, map[j]]|| with D[:, map[j]] = 0; its shift and
+// tolerance are copied from the caller's per-column arrays.
 __global__ void __launch_bounds__(kThreads) m32_init_kernel(int N, const float* __restrict__ R, M32 s,
-                                                           float* __restrict__ D) {
+                                                           float* __restrict__ D, const float* __restrict__ shift_full,
+                                                           const double* __restrict__ tol_full, double tol) {
   __shared__ float red[32];
   const int j = blockIdx.x;
-  const size_t off = (size_t)j * s.ld;
+  const int col = s.map[j];
+  const size_t off = (size_t)j * s.ld, offc = (size_t)col * s.ld;
   float acc = 0.f;
-  for (int a = threadIdx.x; a < N; a += blockDim.x) acc = fmaf(R[off + a], R[off + a], acc);
+  for (int a = threadIdx.x; a < N; a += blockDim.x) acc = fmaf(R[offc + a], R[offc + a], acc);
   const float nrm = sqrtf(block_sum32(acc, red));
   const bool ok = isfinite(nrm) && nrm > 0.f;
   const float inv = ok ? 1.f / nrm : 0.f;
   for (int a = threadIdx.x; a < N; a += blockDim.x) {
-    s.V[off + a] = R[off + a] * inv;
+    s.V[off + a] = R[offc + a] * inv;
     s.Vp[off + a] = 0.f;
     s.W1[off + a] = 0.f;
     s.W2[off + a] = 0.f;
-    D[off + a] = 0.f;
+    D[offc + a] = 0.f;
   }
   if (threadIdx.x == 0) {
     s.beta1[j] = ok ? nrm : 0.0;
@@ -88,10 +98,13 @@ __global__ void __launch_bounds__(kThreads) m32_init_kernel(int N, const float* 
     s.phibar[j] = ok ? nrm : 0.0;
     s.iters[j] = 0;
     s.active[j] = ok ? 1 : 0;
+    s.shift[j] = shift_full[col];
+    s.tolc[j] = tol_full ? tol_full[col] : tol;
+    s.iters_out[col] = 0;
   }
 }
 
-__global__ void __launch_bounds__(kThreads) m32_step_kernel(int N, M32 s, float* __restrict__ D, double tol, int maxit) {
+__global__ void __launch_bounds__(kThreads) m32_step_kernel(int N, M32 s, float* __restrict__ D, int maxit) {
   __shared__ float red[32];
   __shared__ float coef[4];
   const int j = blockIdx.x;
@@ -121,9 +134,9 @@ __global__ void __launch_bounds__(kThreads) m32_step_kernel(int N, M32 s, float*
     s.beta[j] = bnf;
     const int it = s.iters[j] + 1;
     s.iters[j] = it;
+    s.iters_out[s.map[j]] = it;
     const bool bad = !isfinite(bn) || !isfinite(pbn);
-    const double tj = s.tolc ? s.tolc[j] : tol;
-    if (bad || fabs(pbn) <= tj * s.beta1[j] || bn == 0.0 || it >= maxit) s.active[j] = 0;
+    if (bad || fabs(pbn) <= s.tolc[j] * s.beta1[j] || bn == 0.0 || it >= maxit) s.active[j] = 0;
   }
   __syncthreads();
   const float oe = coef[0], de = coef[1], ig = coef[2], ph = coef[3];
@@ -132,7 +145,7 @@ __global__ void __launch_bounds__(kThreads) m32_step_kernel(int N, M32 s, float*
   float* W2 = s.W2 + off;
   float* V = s.V + off;
   float* Vp = s.Vp + off;
-  float* d = D + off;
+  float* d = D + (size_t)s.map[j] * s.ld;
   for (int r = threadIdx.x; r < N; r += blockDim.x) {
     const float v = V[r];
     const float w1 = W1[r];
@@ -143,6 +156,42 @@ __global__ void __launch_bounds__(kThreads) m32_step_kernel(int N, M32 s, float*
     Vp[r] = v;
     V[r] = P[r] * ib;
   }
+}
+
+// Compaction: column k of the new state is column idx[k] of the old one (vectors V, Vp, W1, W2 of
+// N rows; grid (row tiles, n)); the new columns are all active.
+__global__ void m32_gather_vectors_kernel(int N, int n, const int* __restrict__ idx, M32 o, M32 t) {
+  const int k = blockIdx.y;
+  const size_t src = (size_t)idx[k] * o.ld, dst = (size_t)k * t.ld;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
+    t.V[dst + a] = o.V[src + a];
+    t.Vp[dst + a] = o.Vp[src + a];
+    t.W1[dst + a] = o.W1[src + a];
+    t.W2[dst + a] = o.W2[src + a];
+  }
+}
+
+__global__ void m32_gather_scalars_kernel(int n, const int* __restrict__ idx, M32 o, M32 t) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int q = idx[k];
+    t.alpha[k] = o.alpha[q];
+    t.beta[k] = o.beta[q];
+    t.beta1[k] = o.beta1[q];
+    t.cs[k] = o.cs[q];
+    t.sn[k] = o.sn[q];
+    t.dbar[k] = o.dbar[q];
+    t.epsln[k] = o.epsln[q];
+    t.phibar[k] = o.phibar[q];
+    t.tolc[k] = o.tolc[q];
+    t.shift[k] = o.shift[q];
+    t.iters[k] = o.iters[q];
+    t.map[k] = o.map[q];
+    t.active[k] = 1;
+  }
+}
+
+__global__ void iota32_kernel(int* p, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
 }
 
 __global__ void count_active32(const int* __restrict__ active, int n, int* out) {
@@ -560,6 +609,7 @@ constexpr int kChunk = 16;  // steps between convergence checks
 struct ChunkGraph {
   cudaGraphExec_t exec = nullptr;
   long long nodes = 0;
+  bool warm = false;  // a chunk has run eagerly with the current buffers and column count
   ~ChunkGraph() {
     if (exec) cudaGraphExecDestroy(exec);
   }
@@ -567,12 +617,14 @@ struct ChunkGraph {
 
 // Runs n Lanczos steps starting at step it0.  With `graphs`, a full chunk is captured once into a
 // CUDA graph (the step functions launch the same kernels with the same arguments in every chunk:
-// step indices live in device memory) and replayed for every later chunk; the first chunk always
-// runs eagerly, so that one-time work (tile autotuning, workspace growth) happens outside capture.
+// step indices live in device memory) and replayed for every later chunk; the first chunk, and the
+// first after the buffers or the column count change, run eagerly, so that one-time work (tile
+// autotuning, workspace growth) happens outside capture.
 template <class Step>
 acp_status run_chunk(acp_ctx* ctx, ChunkGraph& g, bool graphs, int it0, int n, Step step) {
-  if (!graphs || n != kChunk || it0 == 0) {
+  if (!graphs || n != kChunk || it0 == 0 || !g.warm) {
     for (int i = 0; i < n; ++i) ACP_TRY(step(it0 + i));
+    g.warm = true;
     return ACP_OK;
   }
   if (!g.exec) {
@@ -606,52 +658,107 @@ acp_status run_chunk(acp_ctx* ctx, ChunkGraph& g, bool graphs, int it0, int n, S
 }
 
 // FP32 inner solve of Q(H - s_j)Q D_j = R32_j (R32 projected, unit or zero columns).
-acp_status minres32(acp_ctx* ctx, const float* R32, int ncol, const float* shift32, float* D32, double tol,
-                    const double* tolc, long long* steps, long long* max_it, double t0_ms) {
+// FP32 MINRES on the columns cols[0..n) of the caller's blocks (all ncol columns when cols is
+// null): Q(H - shift32[c])Q D[:, c] = R32[:, c] to the relative tolerance tolc[c] (or tol).  Every
+// chunk of steps, when fewer than 60% of the iterated columns are still active, the state of the
+// active ones is gathered into a second buffer set, so that the spectral, projector and step
+// kernels of the later steps only touch columns that still iterate.
+acp_status minres32(acp_ctx* ctx, const float* R32, int ncol, const int* cols, int n, const float* shift32, float* D32,
+                    double tol, const double* tolc, long long* steps, long long* max_it, double t0_ms) {
   const int N = ctx->N, ld = ctx->ld32;
-  const size_t nv = (size_t)ld * ncol;
-  M32 s{};
-  s.ld = ld;
-  float* vec = nullptr;
-  float* fsc = nullptr;
-  double* dsc = nullptr;
-  int* iv = nullptr;
-  ACP_TRY(ws(ctx, "m32_vec", 5 * nv, &vec));
-  ACP_TRY(ws(ctx, "m32_fsc", 2 * (size_t)ncol, &fsc));
-  ACP_TRY(ws(ctx, "m32_dsc", 6 * (size_t)ncol, &dsc));
-  ACP_TRY(ws(ctx, "m32_iv", 2 * (size_t)ncol, &iv));
-  s.V = vec; s.Vp = vec + nv; s.P = vec + 2 * nv; s.W1 = vec + 3 * nv; s.W2 = vec + 4 * nv;
-  s.alpha = fsc; s.beta = fsc + ncol;
-  s.beta1 = dsc; s.cs = dsc + ncol; s.sn = dsc + 2 * ncol; s.dbar = dsc + 3 * ncol; s.epsln = dsc + 4 * ncol;
-  s.phibar = dsc + 5 * ncol;
-  s.active = iv; s.iters = iv + ncol;
-  s.tolc = tolc;
+  if (n <= 0) return ACP_OK;
+  M32 st[2];
+  for (int b = 0; b < 2; ++b) {
+    const size_t nv = (size_t)ld * n;
+    float* vec = nullptr;
+    float* fsc = nullptr;
+    double* dsc = nullptr;
+    int* iv = nullptr;
+    const char* names[2][4] = {{"m32_vec", "m32_fsc", "m32_dsc", "m32_iv"}, {"m32_vec2", "m32_fsc2", "m32_dsc2", "m32_iv2"}};
+    // the second set is only touched once the first compaction shrinks the problem
+    const size_t nvb = (b == 0) ? nv : (size_t)ld * ((n * 3 + 4) / 5);
+    const size_t nb = (b == 0) ? (size_t)n : (size_t)((n * 3 + 4) / 5);
+    ACP_TRY(ws(ctx, names[b][0], 5 * nvb, &vec));
+    ACP_TRY(ws(ctx, names[b][1], 3 * nb, &fsc));
+    ACP_TRY(ws(ctx, names[b][2], 7 * nb, &dsc));
+    ACP_TRY(ws(ctx, names[b][3], 3 * nb, &iv));
+    M32& s = st[b];
+    s.ld = ld;
+    s.V = vec; s.Vp = vec + nvb; s.P = vec + 2 * nvb; s.W1 = vec + 3 * nvb; s.W2 = vec + 4 * nvb;
+    s.alpha = fsc; s.beta = fsc + nb; s.shift = fsc + 2 * nb;
+    s.beta1 = dsc; s.cs = dsc + nb; s.sn = dsc + 2 * nb; s.dbar = dsc + 3 * nb; s.epsln = dsc + 4 * nb;
+    s.phibar = dsc + 5 * nb; s.tolc = dsc + 6 * nb;
+    s.active = iv; s.iters = iv + nb; s.map = iv + 2 * nb;
+  }
+  int* iters_out = nullptr;
+  ACP_TRY(ws(ctx, "m32_itout", (size_t)ncol, &iters_out));
+  ACP_CUDA(ctx, cudaMemsetAsync(iters_out, 0, sizeof(int) * ncol, ctx->stream));
+  st[0].iters_out = st[1].iters_out = iters_out;
+  if (cols) {
+    ACP_CUDA(ctx, cudaMemcpyAsync(st[0].map, cols, sizeof(int) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  } else {
+    ::acp::note_launch(ctx);
+    iota32_kernel<<<grid_for(n), 256, 0, ctx->stream>>>(st[0].map, n);
+    ACP_LAUNCH(ctx);
+  }
   ::acp::note_launch(ctx);
-  m32_init_kernel<<<ncol, kThreads, 0, ctx->stream>>>(N, R32, s, D32);
+  m32_init_kernel<<<n, kThreads, 0, ctx->stream>>>(N, R32, st[0], D32, shift32, tolc, tol);
   ACP_LAUNCH(ctx);
   const int maxit = ctx->opt.stern_maxit;
   const int period = projection_period(ctx);
+  int cur = 0, ncur = n;
   auto step = [&](int it) -> acp_status {
-    ACP_TRY(spectral32_apply(ctx, s.V, ld, ncol, shift32, s.P, ld, s.alpha, s.active, s.Vp, ld, s.beta));
-    if (it % period == period - 1 || it < 2) ACP_TRY(project32(ctx, s.P, ld, ncol, s.P, ld));
+    M32& s = st[cur];
+    ACP_TRY(spectral32_apply(ctx, s.V, ld, ncur, s.shift, s.P, ld, s.alpha, s.active, s.Vp, ld, s.beta));
+    if (it % period == period - 1 || it < 2) ACP_TRY(project32(ctx, s.P, ld, ncur, s.P, ld));
     ::acp::note_launch(ctx);
-    m32_step_kernel<<<ncol, kThreads, 0, ctx->stream>>>(N, s, D32, tol, maxit);
+    m32_step_kernel<<<ncur, kThreads, 0, ctx->stream>>>(N, s, D32, maxit);
     ACP_LAUNCH(ctx);
     return ACP_OK;
   };
   ChunkGraph graph;
   const bool graphs = ctx->opt.use_graphs && period == 1 && ctx->stream != nullptr;
+  std::vector<int> hact;
   for (int it = 0; it < maxit;) {
-    const int n = (maxit - it < kChunk) ? maxit - it : kChunk;
-    ACP_TRY(run_chunk(ctx, graph, graphs, it, n, step));
-    it += n;
+    const int nstep = (maxit - it < kChunk) ? maxit - it : kChunk;
+    ACP_TRY(run_chunk(ctx, graph, graphs, it, nstep, step));
+    it += nstep;
     int n_act = 0;
-    ACP_TRY(count32(ctx, s.active, ncol, &n_act));
+    ACP_TRY(count32(ctx, st[cur].active, ncur, &n_act));
     if (n_act == 0) break;
     if (deadline_passed(ctx, t0_ms)) return set_error(ctx, ACP_E_TIMEOUT, "deadline passed in FP32 MINRES");
+    if (n_act * 5 < ncur * 3 && it < maxit) {
+      // gather the active columns into the other buffer set (sized 60% of n, enough for them)
+      hact.resize(ncur);
+      ACP_CUDA(ctx, cudaMemcpyAsync(hact.data(), st[cur].active, sizeof(int) * ncur, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+      ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      std::vector<int> idx;
+      idx.reserve(n_act);
+      for (int j = 0; j < ncur; ++j)
+        if (hact[j]) idx.push_back(j);
+      const int nn = (int)idx.size();
+      int* d_idx = nullptr;
+      ACP_TRY(ws(ctx, "m32_cidx", (size_t)(nn > 0 ? nn : 1), &d_idx));
+      ACP_CUDA(ctx, cudaMemcpyAsync(d_idx, idx.data(), sizeof(int) * nn, cudaMemcpyHostToDevice, ctx->stream));
+      const int nxt = 1 - cur;
+      ::acp::note_launch(ctx);
+      m32_gather_vectors_kernel<<<dim3((N + 255) / 256, nn), 256, 0, ctx->stream>>>(N, nn, d_idx, st[cur], st[nxt]);
+      ACP_LAUNCH(ctx);
+      ::acp::note_launch(ctx);
+      m32_gather_scalars_kernel<<<grid_for(nn), 256, 0, ctx->stream>>>(nn, d_idx, st[cur], st[nxt]);
+      ACP_LAUNCH(ctx);
+      cur = nxt;
+      ncur = nn;
+      if (graph.exec) {  // the captured steps name the old buffers and column count
+        cudaGraphExecDestroy(graph.exec);
+        graph.exec = nullptr;
+      }
+      graph.warm = false;  // one eager chunk first: tile autotuning at the new column count
+    }
   }
   ACP_TRY(tc_check(ctx));
-  return sum_iters(ctx, s.iters, ncol, steps, max_it);
+  return sum_iters(ctx, iters_out, ncol, steps, max_it);
 }
 
 // FP64 finish of the columns the FP32 rounds left above their tolerance (stalled, or at the round
@@ -781,7 +888,21 @@ acp_status refine(acp_ctx* ctx, const double* B, int ncol, const double* shift_d
     ACP_TRY(count32(ctx, act, ncol, &n_act));
     if (n_act == 0 || round == kMaxRounds) break;
     if (deadline_passed(ctx, t0_ms)) return set_error(ctx, ACP_E_TIMEOUT, "deadline passed in refinement");
-    ACP_TRY(minres32(ctx, R32, ncol, sh32, D32, kInnerTol, tol_in, &rep->steps, &rep->max_iters, t0_ms));
+    // the inner solve iterates only the columns still refining
+    {
+      std::vector<int> hact(ncol), cols;
+      ACP_CUDA(ctx, cudaMemcpyAsync(hact.data(), act, sizeof(int) * ncol, cudaMemcpyDeviceToHost, ctx->stream));
+      ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      cols.reserve(n_act);
+      for (int j = 0; j < ncol; ++j)
+        if (hact[j]) cols.push_back(j);
+      int* d_cols = nullptr;
+      ACP_TRY(ws(ctx, "rf_cols", (size_t)ncol, &d_cols));
+      ACP_CUDA(ctx, cudaMemcpyAsync(d_cols, cols.data(), sizeof(int) * cols.size(), cudaMemcpyHostToDevice,
+                                    ctx->stream));
+      ACP_TRY(minres32(ctx, R32, ncol, d_cols, (int)cols.size(), sh32, D32, kInnerTol, tol_in, &rep->steps,
+                       &rep->max_iters, t0_ms));
+    }
     ::acp::note_launch(ctx);
     refine_update_kernel<<<grid_for(nv), 256, 0, ctx->stream>>>(N, ncol, ld, D32, scale, act, X);
     ACP_LAUNCH(ctx);

@@ -48,6 +48,8 @@ struct TcArgs {
   float* Y;
   int ldy;
   int* status;
+  uint64_t wait_ns;  // bound of every barrier wait (kWaitNs; shorter in the failure self-test)
+  int withhold;      // failure self-test: the producer issues no TMA load, so no barrier completes
 };
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int n0 = blockIdx.z * p.BN;
   const int kb0 = blockIdx.y * p.kb_per;
   const int nkb = min(p.kb_per, p.kb_total - kb0);
-  const uint64_t deadline = tc::globaltimer_ns() + kWaitNs;
+  const uint64_t deadline = tc::globaltimer_ns() + p.wait_ns;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       bool ok = true;
       int issued = 0;
-      for (int i = 0; i < nkb; ++i) {
+      for (int i = 0; i < (p.withhold ? 0 : nkb); ++i) {
         const int s = i % kStages, u = i / kStages;
         if (u > 0 && !tc::mbar_wait(&empty_bar[s], (u - 1) & 1, deadline)) {
           ok = false;
@@ -121,7 +123,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // no copy may still be landing in shared memory when the CTA exits: wait (bounded) for the
       // last load of every stage; each load completes its stage's full barrier once, so the
       // phase of load i is i / kStages (already complete on the normal path)
-      const uint64_t drain = tc::globaltimer_ns() + kWaitNs;
+      const uint64_t drain = tc::globaltimer_ns() + p.wait_ns;
       for (int i = issued > kStages ? issued - kStages : 0; i < issued; ++i)
         if (!tc::mbar_wait(&full_bar[i % kStages], (uint32_t)(i / kStages) & 1u, drain)) ok = false;
       if (!ok) atomicExch(&abort_sh, 1);
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::tc_fence_after();
     // the MMAs must be done with the accumulator before it is freed (complete on the normal
     // path, where the epilogue has waited for the same phase)
-    if (!tc::mbar_wait(&done_bar, 0, tc::globaltimer_ns() + kWaitNs) && lane == 0) atomicExch(p.status, 1);
+    if (!tc::mbar_wait(&done_bar, 0, tc::globaltimer_ns() + p.wait_ns) && lane == 0) atomicExch(p.status, 1);
     __syncwarp();  // the dealloc is warp-collective (.sync.aligned): reconverge after the wait
     tc::tmem_dealloc(tmem, p.tmem_cols);
   }
@@ -388,6 +390,7 @@ acp_status project32_cfg(acp_ctx* ctx, const float* X, int ldx, int ncol, float*
   a1.ldo = no_pad;
   a1.slice_stride = slice_stride;
   a1.status = status;
+  a1.wait_ns = kWaitNs;
   const double fl = 2.0 * (double)ncol * no * N;  // algorithmic (the tensor pipe runs 3 passes)
   cudaEvent_t ev = prof_begin(ctx);
   ACP_TRY(launch_tc3(ctx, dim3(m_tiles, slices, n_tiles1), mX, mX, mPh, mPl, a1));
@@ -422,6 +425,7 @@ acp_status project32_cfg(acp_ctx* ctx, const float* X, int ldx, int ncol, float*
   a2.Y = Y;
   a2.ldy = ldy;
   a2.status = status;
+  a2.wait_ns = kWaitNs;
   ev = prof_begin(ctx);
   ACP_TRY(launch_tc3(ctx, dim3(m_tiles, 1, (N + bn2 - 1) / bn2), mCh, mCl, mTh, mTl, a2));
   prof_end(ctx, "tc_gemm", ev, fl, 4.0 * (2.0 * ncol * N + 2.0 * no * N + 2.0 * (double)ncol * no_pad));
@@ -508,6 +512,45 @@ acp_status project_mixed64(acp_ctx* ctx, const double* X, int ncol, double* Y) {
   ::acp::note_launch(ctx);
   widen_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(N, ncol, ld, x32, Y);
   ACP_LAUNCH(ctx);
+  return tc_check(ctx);
+}
+
+// Failure self-test of the bounded waits: GEMM 1 of the projector on a zero block of 128 columns
+// with its TMA loads withheld, so the split warps' and the MMA warp's barrier waits run out after
+// wait_ns; the kernel then skips its MMAs and epilogue, waits (bounded) for the empty commit,
+// frees its TMEM, sets the status word and returns.  Returns what tc_check reports
+// (ACP_E_TIMEOUT when the abort path ran).
+acp_status tc_selftest_timeout(acp_ctx* ctx, uint64_t wait_ns) {
+  ACP_TRY(mixed_prepare(ctx));
+  const int N = ctx->N, no = ctx->n_orb, no_pad = ctx->no_pad, ld = ctx->ld32;
+  const int ncol = kBM;
+  float *x = nullptr, *part = nullptr;
+  ACP_TRY(ws(ctx, "st_x", (size_t)ld * ncol, &x));
+  ACP_TRY(ws(ctx, "st_part", (size_t)ncol * no_pad, &part));
+  ACP_CUDA(ctx, cudaMemsetAsync(x, 0, sizeof(float) * ld * ncol, ctx->stream));
+  const int n_tiles1 = (no + 255) / 256;
+  int bn1 = (no + n_tiles1 - 1) / n_tiles1;
+  bn1 = (bn1 + 15) / 16 * 16;
+  CUtensorMap mX, mPh, mPl;
+  ACP_TRY(make_map(ctx, &mX, x, N, ncol, ld, kBM));
+  ACP_TRY(make_map(ctx, &mPh, ctx->d_psi_hi, N, no, ld, bn1));
+  ACP_TRY(make_map(ctx, &mPl, ctx->d_psi_lo, N, no, ld, bn1));
+  TcArgs a{};
+  a.M = ncol;
+  a.Nd = no;
+  a.BN = bn1;
+  a.kb_total = (N + kBK - 1) / kBK;
+  a.kb_per = a.kb_total;
+  a.tmem_cols = tmem_cols_for(bn1);
+  a.split_a = 1;
+  a.mode = 0;
+  a.out = part;
+  a.ldo = no_pad;
+  a.slice_stride = (long long)ncol * no_pad;
+  a.status = ctx->d_flag + 8;
+  a.wait_ns = wait_ns;
+  a.withhold = 1;
+  ACP_TRY(launch_tc3(ctx, dim3(1, 1, n_tiles1), mX, mX, mPh, mPl, a));
   return tc_check(ctx);
 }
 
