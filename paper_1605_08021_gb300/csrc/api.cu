@@ -93,6 +93,13 @@ void prof_end(acp_ctx* ctx, const char* name, cudaEvent_t begin, double flops, d
   p.pending.push_back({name, begin, e, flops, bytes});
 }
 
+void prof_amend_last(acp_ctx* ctx, const char* name, double flops, double bytes) {
+  Profiler& p = ctx->prof;
+  if (!p.on || p.pending.empty() || std::strcmp(p.pending.back().name, name) != 0) return;
+  p.pending.back().flops = flops;
+  p.pending.back().bytes = bytes;
+}
+
 void prof_flush(acp_ctx* ctx) {
   Profiler& p = ctx->prof;
   if (p.pending.empty()) {

@@ -150,6 +150,8 @@ cudaEvent_t prof_begin(acp_ctx* ctx);
 void prof_end(acp_ctx* ctx, const char* name, cudaEvent_t begin, double flops, double bytes);
 // Accumulates the elapsed times of completed launches (the stream must be synchronised).
 void prof_flush(acp_ctx* ctx);
+// Sets the work of the last recorded launch of `name` (known only after the launch completes).
+void prof_amend_last(acp_ctx* ctx, const char* name, double flops, double bytes);
 
 // ---- host wrappers of the kernels (one translation unit each) -------------------------------
 // spectral.cu

@@ -712,8 +712,12 @@ acp_status minres32(acp_ctx* ctx, const float* R32, int ncol, const int* cols, i
     ACP_TRY(spectral32_apply(ctx, s.V, ld, ncur, s.shift, s.P, ld, s.alpha, s.active, s.Vp, ld, s.beta));
     if (it % period == period - 1 || it < 2) ACP_TRY(project32(ctx, s.P, ld, ncur, s.P, ld));
     ::acp::note_launch(ctx);
+    cudaEvent_t ev0 = prof_begin(ctx);
     m32_step_kernel<<<ncur, kThreads, 0, ctx->stream>>>(N, s, D32, maxit);
     ACP_LAUNCH(ctx);
+    // per iterated column: P read, V, W1, W2, D read and V, Vp, W1, W2, D written (FP32); columns
+    // that converged inside the chunk return early, so this counts at most the bytes moved
+    prof_end(ctx, "m32_step", ev0, 0.0, 40.0 * N * (double)ncur);
     return ACP_OK;
   };
   ChunkGraph graph;
@@ -1016,8 +1020,11 @@ acp_status minres_multishift_mixed(acp_ctx* ctx, const double* B, int nmu, const
                              (int)s.slot_ld, s.beta, kdev, ld));
     if (k0 % period == period - 1 || k0 < 2) ACP_TRY(project32(ctx, s.P, ld, nmu, s.P, ld));
     ::acp::note_launch(ctx);
+    cudaEvent_t ev0 = prof_begin(ctx);
     msb32_step_kernel<<<nmu, kThreads, 0, ctx->stream>>>(N, nc, kdev, s, kInnerTol);
     ACP_LAUNCH(ctx);
+    // per selected point: P read and the next basis vector written (FP32)
+    prof_end(ctx, "msb32_step", ev0, 0.0, 8.0 * N * (double)nmu);
     ::acp::note_launch(ctx);
     advance_k_kernel<<<1, 1, 0, ctx->stream>>>(kdev);
     ACP_LAUNCH(ctx);

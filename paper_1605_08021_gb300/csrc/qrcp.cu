@@ -604,12 +604,21 @@ acp_status compress(acp_ctx* ctx, const double* G, int ncol, const double* sketc
     ACP_CUDA(ctx, cudaMemsetAsync(pa.status, 0, 4 * sizeof(int), ctx->stream));
     void* kargs[] = {&pa};
     ::acp::note_launch(ctx);
+    cudaEvent_t ev0 = prof_begin(ctx);
     ACP_CUDA(ctx, cudaLaunchCooperativeKernel(pq_fn, dim3(n_sm), dim3(pq_threads), kargs, pq_smem, ctx->stream));
+    prof_end(ctx, "qrcp", ev0, 0.0, 0.0);
     int hs[2] = {0, 0};
     ACP_CUDA(ctx, cudaMemcpyAsync(hs, pa.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     ACP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (hs[1]) return set_error(ctx, ACP_E_TIMEOUT, "pivoted QR: a grid barrier of the persistent kernel timed out");
     k = hs[0];
+    {
+      // algorithmic work of the k steps: the reflector's dot product and update on the trailing
+      // (m - j) x (N - j - 1) block, 2 FMAs and one read and one write of each FP64 element
+      double el = 0.0;
+      for (int j = 0; j < k; ++j) el += (double)(m - j) * (double)(N - j - 1);
+      prof_amend_last(ctx, "qrcp", 4.0 * el, 16.0 * el);
+    }
     if (k <= 0) return set_error(ctx, ACP_E_RANK, "pivoted QR found rank 0 (is G zero?)");
     out->n_mu = k;
     out->piv.resize(N);
