@@ -2,7 +2,7 @@
 """Benchmark: Sternheimer (shift, right-hand side) pairs solved per second and dynamical-matrix
 time of the ACP method on one GB300, on the 1D rHF chain of 128 atoms (N = 5120 grid points,
 mixed charges Z in {1, 2}, 192 occupied orbitals, 128 perturbations).  The timed settings (20
-Chebyshev nodes, id_tol 1e-9, Alg. 4 delta 1e-9) are the cheapest tried that meet the 1e-5
+Chebyshev nodes, id_tol 1e-9, Alg. 4 delta 1e-8) are the cheapest tried that meet the 1e-5
 relative phonon-frequency bar against the oracle's exact D; the configuration's own 16 nodes miss
 it (error 5e-5) and are reported as a labelled comparison.
 
@@ -37,7 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Sternheimer RHS solved/s and dynamical-matrix time, ACP forms vs plain FP64, 1 GB300"
 UNIT = "RHS/s"
 CONFIG = 2
-ACP_PARAMS = dict(id_tol=1e-9, n_cheb=20, sketch_r=8, dyson_tol=1e-9, dyson_maxit=20, stern_tol=1e-11)
+ACP_PARAMS = dict(id_tol=1e-9, n_cheb=20, sketch_r=8, dyson_tol=1e-8, dyson_maxit=20, stern_tol=1e-11)
 # the configuration's stated node count (misses the 1e-5 bar; a labelled comparison figure)
 CONFIG_STATED = dict(id_tol=1e-8, n_cheb=16, dyson_tol=1e-6)
 # selected points of the first Alg. 4 iteration whose compressed solves one oracle sample times

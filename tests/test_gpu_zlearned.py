@@ -146,3 +146,38 @@ def test_training_on_another_grid():
     assert abs(loss - Lo) <= 1e-5 * Lo
     assert rel(g.astype(np.float64), np.concatenate([np.concatenate([dW.ravel(), db]) for dW, db in go])) < 1e-4
     assert np.array_equal(ctx.cnn_get_weights(), w)  # lr = 0 leaves the weights as they were
+
+
+def test_trained_guess_cuts_krylov_steps():
+    """The network trained on this library's own solutions (paper_1605_08021_gb300/weights, 200
+    seeded lattices; the run's record is cnn_x0.json beside the weights) starts the solves of a
+    lattice held out of training closer to the solution: fewer Lanczos steps than from zero, to the
+    same stern_tol (1e-8) checked as a true FP64 residual of the oracle's operator, and the same
+    solutions."""
+    import os
+
+    import torch
+
+    import paper_1605_08021_gb300 as P
+    from oracle.chi0 import sternheimer_operator
+    from oracle.model import Model2D
+    from paper_1605_08021_gb300.train_cnn import _context, _samples
+    wdir = os.path.join(os.path.dirname(P.__file__), "weights")
+    w = np.load(os.path.join(wdir, "cnn_x0.npy"))
+    s = W.training_lattices(1, first=203)[0]  # systems 200-207 were held out of the training run
+    gs = W.ground_state(s, tol=1e-8)
+    rng = np.random.default_rng(7)
+    R, _, X0, shifts, st0 = _samples(P, s, gs, 32, rng, 1e-8)
+    ctx = _context(P, s, gs, stern_tol=1e-8, learned=1)
+    ctx.cnn_set_weights(w)
+    X1, st1 = ctx.sternheimer_solve(R, shifts)
+    torch.cuda.synchronize()
+    assert st0["rhs_solved"] == 32 and st1["rhs_solved"] == 32
+    assert st1["lanczos_steps"] <= 0.97 * st0["lanczos_steps"], (st1["lanczos_steps"], st0["lanczos_steps"])
+    m = Model2D(s, gs)
+    A = sternheimer_operator(m)
+    Rn, X0n, X1n = to_np(R), to_np(X0), to_np(X1)
+    for X in (X0n, X1n):
+        res = np.linalg.norm(A(X, shifts) - Rn, axis=0) / np.linalg.norm(Rn, axis=0)
+        assert res.max() < 2e-8
+    assert rel(X1n, X0n) < 1e-6
