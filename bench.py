@@ -538,7 +538,7 @@ def run_gpu_batch(args):
                                "640-10240 points), Z in {1,2}, kernel scale 0.3-1.0; ACP mixed precision per system "
                                f"(N_c={ACP_PARAMS['n_cheb']}, id_tol={ACP_PARAMS['id_tol']:g}, "
                                f"delta={ACP_PARAMS['dyson_tol']:g}); batched over {workers} worker threads, "
-                               "one stream per system, CUDA-graph replay",
+                               "one stream per worker, CUDA-graph replay",
                    "l2": "working set larger than L2", "parallelism": f"replicas x{world}"},
         "systems": len(systems), "grid_points_total": int(sum(sy.n[0] for sy in systems)),
         "statuses_ok": sum(1 for x in statuses if x == "ACP_OK"),

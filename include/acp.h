@@ -187,19 +187,21 @@ acp_status acp_dynamical_matrix(acp_ctx* ctx, const acp_atoms* atoms, const doub
                                 double* D_h, double* U_d, acp_stats* stats);
 
 /* Batched form: the dynamical matrices of n_sys independent systems of uneven size, one context
-   per system (created by the caller, each on its own CUDA stream so that the systems run
-   concurrently; contexts sharing a stream serialise).  A pool of n_workers host threads (0: one
-   per hardware thread, at most 64) takes systems from a work queue, largest grid first, and runs
-   acp_dynamical_matrix on each: the per-system phases (compression, Alg. 4 updates, D) of
-   different systems overlap on their streams, and with use_graphs set in the contexts' options
-   every 16-step chunk of the FP32 Lanczos loops is one CUDA graph launch.  atoms[i], rho_d[i],
-   D_h[i] and stats[i] (nullable) are system i's arguments of acp_dynamical_matrix;
-   status_out (nullable, n_sys entries) receives each system's status.  Each worker carries one
-   set of device workspace buffers from system to system (the contexts' own buffers join it and
-   every context leaves the batch without workspace), so the batch holds memory only for the
-   systems in flight and allocates only when a larger system needs more.  Returns ACP_OK, or the first
-   failing system's status (the others still run).  No counterpart in the paper, which treats
-   one system at a time. */
+   per system.  A pool of n_workers host threads (0: one per hardware thread, at most 64) takes
+   systems from a work queue, largest grid first, and runs acp_dynamical_matrix on each, on a CUDA
+   stream owned by the worker (the batch first waits for the work pending on the context's own
+   stream, and the context gets its stream back afterwards), so that the per-system phases
+   (compression, Alg. 4 updates, D) of different systems overlap even when the callers' contexts
+   share a stream; with use_graphs set in the contexts' options every 16-step chunk of the FP32
+   Lanczos loops is one CUDA graph launch.  atoms[i], rho_d[i], D_h[i] and stats[i] (nullable) are
+   system i's arguments of acp_dynamical_matrix; status_out (nullable, n_sys entries) receives each
+   system's status.  Each worker carries one set of device workspace buffers from system to system
+   (the contexts' own buffers join it and every context leaves the batch without workspace).  A
+   system enters only while the estimated workspace of the systems in flight fits in 85% of the
+   device memory free at the start (one system always runs); a worker that waits, or moves on to a
+   much smaller system, gives its buffers back; a system that still runs out of memory beside
+   others is run again alone at the end.  Returns ACP_OK, or the first failing system's status (the
+   others still run).  No counterpart in the paper, which treats one system at a time. */
 acp_status acp_batch_dynamical_matrix(acp_ctx* const* ctxs, int n_sys, const acp_atoms* atoms,
                                       const double* const* rho_d, double* const* D_h, acp_stats* stats,
                                       acp_status* status_out, int n_workers);

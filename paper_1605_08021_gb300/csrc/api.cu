@@ -3,6 +3,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
 #include <mutex>
 #include <thread>
@@ -484,14 +485,67 @@ acp_status acp_batch_dynamical_matrix(acp_ctx* const* ctxs, int n_sys, const acp
   // flight only and allocates (cudaMalloc / cudaFree synchronise the device) only when a larger
   // system needs more; what the workers hold at the end is freed.
   std::vector<std::map<std::string, std::pair<void*, size_t>>> held(workers);
+  // Each worker runs its systems on a stream of its own.  The callers' streams may coincide (a
+  // pool of library streams can hand the same one to several contexts), and a worker that captures
+  // its Lanczos steps as a CUDA graph must not see another worker's launches on the same stream.
+  std::vector<cudaStream_t> wstream(workers, nullptr);
+  for (int w = 0; w < workers; ++w)
+    if (cudaStreamCreateWithFlags(&wstream[w], cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      for (int v = 0; v < w; ++v) cudaStreamDestroy(wstream[v]);
+      return ACP_E_CUDA;
+    }
+  // Admission by device memory: a system enters only while the workspace estimates of the systems
+  // in flight fit in 85% of the memory free at the start (one system always runs).  Estimate, per
+  // grid point and (shift, point) pair of the N_c x N_mu Sternheimer equations (N_mu ~ 7 n_orb):
+  // four FP64 blocks (solutions, replicated right-hand sides, residuals, operator products) and ten
+  // FP32 ones (refinement residual and correction, the MINRES vectors and their compacted copy),
+  // 72 bytes with 1/8 allocation headroom, plus the stored FP32 Lanczos basis (512 steps, at most
+  // 16 GB).  A system that still runs out of memory is run again alone after the others.
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const double budget = 0.85 * (double)free_b;
+  std::vector<double> need(n_sys);
+  for (int i = 0; i < n_sys; ++i) {
+    const acp_ctx* c = ctxs[i];
+    const double nmu = 7.0 * c->n_orb, nc = c->opt.n_cheb > 0 ? c->opt.n_cheb : 16;
+    need[i] = 81.0 * c->N * nc * nmu + std::min(16.0e9, 512.0 * 4.0 * c->N * nmu);
+  }
+  std::mutex adm_mu;
+  std::condition_variable adm_cv;
+  double in_flight = 0.0;
+  int running = 0;
+  auto release_held = [&](int w) {
+    std::lock_guard<std::mutex> lock(device_mutex());
+    for (auto& kv : held[w])
+      if (kv.second.first) cudaFree(kv.second.first);
+    held[w].clear();
+  };
   auto worker = [&](int w) {
     for (;;) {
       const int q = next.fetch_add(1);
       if (q >= n_sys) return;
       const int i = order[q];
       acp_ctx* c = ctxs[i];
+      {
+        // buffers kept from a larger system would exceed this system's estimate: give them back
+        double held_b = 0.0;
+        for (const auto& kv : held[w]) held_b += (double)kv.second.second;
+        if (held_b > 1.25 * need[i]) release_held(w);
+        std::unique_lock<std::mutex> lk(adm_mu);
+        if (!(running == 0 || in_flight + need[i] <= budget)) {
+          lk.unlock();
+          release_held(w);  // waiting: give the memory back to the systems in flight
+          lk.lock();
+          adm_cv.wait(lk, [&] { return running == 0 || in_flight + need[i] <= budget; });
+        }
+        in_flight += need[i];
+        ++running;
+      }
       cudaSetDevice(c->device);
-      cudaStreamSynchronize(c->stream);
+      cudaStreamSynchronize(c->stream);  // the caller's inputs are ready
+      cudaStream_t caller_stream = c->stream;
+      c->stream = wstream[w];
       for (auto& kv : c->ws.bufs) {  // the context's own buffers join the worker's set
         auto it = held[w].find(kv.first);
         if (it == held[w].end() || it->second.second < kv.second.second) {
@@ -511,22 +565,46 @@ acp_status acp_batch_dynamical_matrix(acp_ctx* const* ctxs, int n_sys, const acp
       c->tables32_stale = true;
       st[i] = acp_dynamical_matrix(c, &atoms[i], rho_d[i], D_h[i], nullptr, stats ? &stats[i] : nullptr);
       cudaStreamSynchronize(c->stream);
+      c->stream = caller_stream;
       held[w] = std::move(c->ws.bufs);
       c->ws.bufs.clear();
       c->psi32_stale = true;
       c->tables32_stale = true;
+      {
+        std::lock_guard<std::mutex> lk(adm_mu);
+        in_flight -= need[i];
+        --running;
+      }
+      adm_cv.notify_all();
     }
   };
   std::vector<std::thread> pool;
   for (int w = 1; w < workers; ++w) pool.emplace_back(worker, w);
   worker(0);
   for (auto& t : pool) t.join();
+  for (int w = 0; w < workers; ++w) release_held(w);
+  auto destroy_streams = [&]() {
+    for (cudaStream_t x : wstream)
+      if (x) cudaStreamDestroy(x);
+  };
+  // systems that ran out of memory beside others run again, one at a time, largest first
   {
-    std::lock_guard<std::mutex> lock(device_mutex());
-    for (auto& h : held)
-      for (auto& kv : h)
-        if (kv.second.first) cudaFree(kv.second.first);
+    std::vector<int> retry;
+    for (int q = 0; q < n_sys; ++q)
+      if (st[order[q]] == ACP_E_OOM) retry.push_back(order[q]);
+    if (!retry.empty()) {
+      next.store(0);
+      std::vector<int> saved = order;
+      order = retry;
+      const int saved_n = n_sys;
+      n_sys = (int)retry.size();
+      worker(0);
+      release_held(0);
+      order = saved;
+      n_sys = saved_n;
+    }
   }
+  destroy_streams();
   acp_status worst = ACP_OK;
   for (int i = 0; i < n_sys; ++i) {
     if (status_out) status_out[i] = st[i];
