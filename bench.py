@@ -283,7 +283,8 @@ def run_gpu(args):
     peaks, peak_src = load_peaks()
     rows = roofline_rows(prof, ms, peaks, peak_src)
     roof = dict(max(rows, key=lambda r: r["ms"]))
-    roof["families"] = [{k: r[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "share_of_step")}
+    roof["families"] = [{k: r[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac", "share_of_step",
+                                           "traffic", "algorithmic_bytes_per_launch")}
                         for r in sorted(rows, key=lambda r: -r["ms"]) if r["share_of_step"] >= 0.05]
     roof["kernel_ms"] = {k: round(v["ms"], 2) for k, v in prof.items()}
     st = stats[-1]
@@ -346,6 +347,16 @@ FAMILY_INFO = {
     "m32_step": ("hbm", "m32_step_kernel (FP32 MINRES update of the refinement solves)"),
     "msb32_step": ("hbm", "msb32_step_kernel (FP32 multi-shift step: basis vector and per-shift Givens)"),
 }
+# DRAM bytes (read + write) per launch from the ncu captures of `python -m
+# paper_1605_08021_gb300.profile_step` (this workload, one step; the summaries in profiles/ give
+# the launch each figure belongs to).  Set to None once a kernel changes after its capture.
+TRAFFIC = {
+    "dgemm": (1.371e8, "mean of the first 80 dgemm_kernel launches of a step (profiles/dgemm_c2_dram.md)"),
+    "qrcp": (1.322e11, "one launch, 1116 pivots of the 3072 x 5120 sketch (profiles/qr_persistent_c2.md)"),
+    "spectral32": (4.76e7, "one launch over 1116 columns (profiles/spectral32_c2.md)"),
+    "tc_gemm": (3.16e7, "GEMM 1 + GEMM 2 mean over one projector application, 1116 columns (profiles/tc3_gemm_c2.md)"),
+    "m32_step": (4.978e9, "one launch over 24460 columns (profiles/m32_step_c2.md)"),
+}
 # FP64 DFMA rate from the GB300 unit count and clock: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -367,8 +378,12 @@ def roofline_rows(prof, step_ms_total, peaks, peak_src):
         else:
             achieved, peak, unit = p["bytes"] / (p["ms"] * 1e-3) / 1e9, float(peaks["hbm_gbs"]), "GB/s"
             src = f"hbm_gbs of {peak_src}"
+        tr = TRAFFIC.get(k)
         rows.append({"bound": bound, "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": unit,
-                     "frac": round(achieved / peak, 4), "traffic": None, "kernel": name, "peak_source": src,
+                     "frac": round(achieved / peak, 4), "traffic": tr[0] if tr else None,
+                     "traffic_launch": tr[1] if tr else None,
+                     "algorithmic_bytes_per_launch": round(p["bytes"] / p["launches"]) if p["launches"] else None,
+                     "kernel": name, "peak_source": src,
                      "ms": p["ms"], "share_of_step": round(p["ms"] / step_ms_total, 4) if step_ms_total > 0 else None,
                      "launches": p["launches"]})
     return rows

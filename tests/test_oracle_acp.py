@@ -118,7 +118,9 @@ def test_table1_capped_rank_cell():
     with the rank fixed below what the threshold of Table 2 selects.  The truncation dominates that
     cell (the Chebyshev error of 5 nodes is 4e-3 on this chain), so it pins the compression, the
     weights of Eq. eqnW and the update of Eq. dyson4 together.  Two Alg. 4 iterations settle it
-    (the second changes U by 5e-3 and the error by < 5%)."""
+    (the second changes U by 5e-3 and the error by < 5%).  The compressed equations are solved
+    exactly in the eigenbasis of the grid Hamiltonian (pinned against MINRES in
+    test_oracle_sec41.py)."""
     import json
     import os
     golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_table1.json")))
@@ -129,7 +131,7 @@ def test_table1_capped_rank_cell():
     G, _ = m.perturbations()
     Ud = Dy.dyson_dense(m, G)
     om = W.srft_sketch(G.shape[1], 8, 0)
-    U, _ = A.chi_acp(m, G, om, 0.0, 5, delta=0.0, maxit=2, tol=1e-8, max_rank=3 * m.n_orb)
+    U, _ = A.chi_acp(m, G, om, 0.0, 5, delta=0.0, maxit=2, max_rank=3 * m.n_orb, spectrum=C.full_spectrum(m))
     err = np.linalg.norm(U - Ud) / np.linalg.norm(Ud)
     paper = golden["rows"]["5"][0]
     assert abs(err / paper - 1.0) < 0.25, err
