@@ -332,7 +332,14 @@ acp_status acp_build(acp_ctx* ctx, const double* Gk, int ncol, Compression* comp
   ACP_TRY(ws(ctx, "acp_x", (size_t)N * k * nc, &X));
   const double ts = now_ms();
   ACP_TRY(minres_multishift(ctx, rhs, k, nodes, nc, X, rep, t0));
-  ACP_TRY(project(ctx, X, N, k * nc, X, N));  // zeta lies in the unoccupied space
+  // zeta lies in the unoccupied space: the outer Q of Eq. eqncompressU.  An inexact Alg. 4
+  // iteration of the mixed form (FP32 solves only, relative error ~1e-6) takes Q through the
+  // tensor-core projector, accurate to FP32 like the solves; solutions refined to stern_tol take
+  // the FP64 one.
+  if (ctx->opt.precision == ACP_PREC_MIXED && !ctx->mixed_refine)
+    ACP_TRY(project_mixed64(ctx, X, k * nc, X));
+  else
+    ACP_TRY(project(ctx, X, N, k * nc, X, N));
   if (ms_solve) *ms_solve += now_ms() - ts;
   // W = sum_c (-2f) X_c .* (Psi diag(L_c) Psi(r_mu, :)^T)   (Eq. eqnW, zeta = -x)
   ACP_TRY(ws(ctx, "acp_w", (size_t)N * k, &W));
