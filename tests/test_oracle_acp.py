@@ -157,3 +157,19 @@ def test_full_srft_of_M(small):
         assert np.allclose(comp.Xi[comp.pivots, :], np.eye(comp.pivots.size), atol=1e-12)
         Mrec = comp.Xi @ M[comp.pivots, :]
         assert np.linalg.norm(M - Mrec) <= 100 * eps * np.linalg.norm(M)
+
+
+def test_interpolation_vectors_are_the_least_squares_fit(small):
+    """Alg. 2 step 4 written as a least-squares fit: with M_tilde^T Pi = Q R, the interpolation
+    vectors Xi^T = R_11^{-1} [R_11 R_12] Pi^{-1} equal the least-squares solution of
+    min ||M_tilde - Xi M_tilde(r_mu, :)||_F, i.e. Xi = M_tilde M_tilde(r_mu, :)^+ (M_tilde(r_mu, :) has
+    full row rank N_mu).  Checked against numpy's lstsq on the sketched rows, below and at full rank."""
+    s, gs, m, Cm, G = small
+    Om = W.srft_sketch(G.shape[1], 4, 3)
+    MT = A.sketch_rows(m, G, Om)                  # M_tilde^T: (r N_e) x N_g
+    Mt = MT.T
+    for eps in (1e-3, 1e-8):
+        comp = A.interpolative_decomposition(m, G, Om, eps)
+        Msel = Mt[comp.pivots, :]                  # N_mu x (r N_e)
+        XiT_ls, *_ = np.linalg.lstsq(Msel.T, Mt.T, rcond=None)
+        assert np.abs(XiT_ls.T - comp.Xi).max() <= 1e-8 * max(1.0, np.abs(comp.Xi).max())
