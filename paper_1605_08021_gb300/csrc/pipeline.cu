@@ -395,15 +395,20 @@ acp_status dyson_acp(acp_ctx* ctx, const double* G, int ncol, double* U, acp_sta
   // Mixed precision: while the iterates still change by more than kRefineSwitch, the compressed
   // equations are solved by the FP32 pass alone (an inexact outer iteration, whose error ~1e-6
   // is below the change); from then on every solve is refined to stern_tol, and Alg. 4 may only
-  // stop after a refined iteration.
+  // stop after a refined iteration.  An FP32-only iteration that shrinks the change by less than
+  // 2x has met the noise floor of its solves (above kRefineSwitch when Alg. 4 amplifies them):
+  // refinement then starts at once.
   constexpr double kRefineSwitch = 1e-4;
+  bool refining = false;
+  double prev_change = 1e300;
   const bool mixed = ctx->opt.precision == ACP_PREC_MIXED;
   struct RefineReset {
     acp_ctx* c;
     ~RefineReset() { c->mixed_refine = true; }
   } reset{ctx};
   for (it = 0; it < maxit; ++it) {
-    ctx->mixed_refine = !mixed || change <= kRefineSwitch || it == maxit - 1;
+    refining = refining || change <= kRefineSwitch || (it >= 2 && change > 0.5 * prev_change) || it == maxit - 1;
+    ctx->mixed_refine = !mixed || refining;
     ACP_TRY(spectral_apply(ctx, Ut, N, ncol, MULT_KHAT, false, nullptr, Gk, N, nullptr, nullptr));
     Compression comp;
     double* W = nullptr;
@@ -426,6 +431,7 @@ acp_status dyson_acp(acp_ctx* ctx, const double* G, int ncol, double* U, acp_sta
     ACP_TRY(dgemm(ctx, false, false, N, ncol, k, 1.0, W, N, Y, k, 1.0, Un, N));
     double nrm[2];
     ACP_TRY(diff_norms(ctx, Un, Ut, nv, nrm));
+    prev_change = change;
     change = nrm[1] > 0 ? sqrt(nrm[0] / nrm[1]) : 0.0;
     double* t = Ut; Ut = Un; Un = t;
     if (st) st->n_mu = k;
